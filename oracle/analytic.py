@@ -1,0 +1,73 @@
+"""Closed-form results the paper compares its method with, restated for use
+as pins of the oracle.  TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+"""
+import numpy as np
+from scipy import integrate, special
+
+
+def bessel_wave(rho1_0, R, ck, t, r, n_terms=400):
+    """Cylindrical wave solution, Eq. (analyticdensityprop):
+    rho1(r, t) = 2/R^2 sum_n J0(k_n r/R) cos(c_k k_n t / R) / J1(k_n)^2
+                 * integral_0^R rho1(r', 0) J0(k_n r'/R) r' dr',
+    with k_n the zeros of J0.  rho1_0 is a callable of r'."""
+    kn = special.jn_zeros(0, n_terms)
+    r = np.asarray(r, dtype=np.float64)
+    out = np.zeros_like(r)
+    rr = np.linspace(0.0, R, 8001)
+    f0 = rho1_0(rr)
+    for k in kn:
+        coef = integrate.simpson(f0 * special.j0(k * rr / R) * rr, x=rr)
+        out += coef * special.j0(k * r / R) * np.cos(ck * k * t / R) / special.j1(k) ** 2
+    return 2.0 / R**2 * out
+
+
+def miller_scriven_omega2(sigma, R0, rho_l, rho_v, nu_l, nu_v, lam=1.0):
+    """Mode-2 angular frequency of a viscous droplet, Eq. (oscillatingfreq):
+    omega2 = omega* - alpha sqrt(omega*)/2 + alpha^2/4 with
+    omega* = sqrt(24 lam sigma / (R0^3 (2 rho_v + 3 rho_l))) and
+    alpha = 25 sqrt(nu_l nu_v) rho_l rho_v /
+            (sqrt(2) R0 (2 rho_v + 3 rho_l)(sqrt(nu_l) rho_l + sqrt(nu_v) rho_v))."""
+    w_star = np.sqrt(24.0 * lam * sigma / (R0**3 * (2.0 * rho_v + 3.0 * rho_l)))
+    alpha = (25.0 * np.sqrt(nu_l * nu_v) * rho_l * rho_v) / (
+        np.sqrt(2.0) * R0 * (2.0 * rho_v + 3.0 * rho_l) * (np.sqrt(nu_l) * rho_l + np.sqrt(nu_v) * rho_v)
+    )
+    return w_star - alpha * np.sqrt(w_star) / 2.0 + alpha**2 / 4.0
+
+
+def hagen_poiseuille(g, R, nu, r):
+    """Steady axial pipe flow driven by a body acceleration g: u_z = g (R^2 - r^2) / (4 nu)."""
+    return g * (R**2 - np.asarray(r) ** 2) / (4.0 * nu)
+
+
+def plane_poiseuille(g, R, nu, r):
+    """Same drive in plane (2D) geometry with a symmetry line at r = 0: u = g (R^2 - r^2) / (2 nu)."""
+    return g * (R**2 - np.asarray(r) ** 2) / (2.0 * nu)
+
+
+def fit_damped_cosine(t, y):
+    """Least-squares fit y = a + b exp(-c t) cos(w t + d); returns (w, c)."""
+    from scipy import optimize
+
+    t = np.asarray(t, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    yc = y - y.mean()
+    # initial frequency from zero crossings
+    s = np.sign(yc)
+    idx = np.nonzero(s[1:] * s[:-1] < 0)[0]
+    if len(idx) >= 2:
+        w0 = np.pi / np.mean(np.diff(t[idx]))
+    else:
+        w0 = 2 * np.pi / (t[-1] - t[0])
+    a0, b0 = y.mean(), (y.max() - y.min()) / 2
+
+    def model(p, tt):
+        a, b, c, w, d = p
+        return a + b * np.exp(-c * tt) * np.cos(w * tt + d)
+
+    best = None
+    for d0 in np.linspace(0, 2 * np.pi, 8, endpoint=False):
+        res = optimize.least_squares(lambda p: model(p, t) - y, [a0, b0, 0.0, w0, d0])
+        if best is None or res.cost < best.cost:
+            best = res
+    a, b, c, w, d = best.x
+    return abs(w), c
