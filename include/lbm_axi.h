@@ -1,0 +1,189 @@
+/*
+ * lbm_axi.h — C ABI of the GB300 (sm_103a) axisymmetric multiphase lattice
+ * Boltzmann engine.
+ *
+ * The method is the axisymmetric pseudopotential D2Q9 scheme of Reijers,
+ * Gelderblom & Toschi, "Axisymmetric multiphase lattice Boltzmann method for
+ * generic equations of state" (arXiv:1512.01977):
+ *   - BGK evolution with a source term, Sec. II.A, Eq. (lbm);
+ *   - Srivastava-type axisymmetric source h_i with H_z, H_r, Sec. II.B, Eq. (axihz);
+ *   - pseudopotential psi = sqrt(rho/3 - P_k(rho)) and the Kupershtokh
+ *     single-neighbour force with mixing parameter A, applied by the exact
+ *     difference method (EDM), Sec. II.C, Eq. (kupershtokhforcing);
+ *   - the cylindrical multiphase correction F_axis, Eq. (multiphasecorrections),
+ *     with the isotropic finite differences of Eq. (fifthorderaccuratefinitedifference);
+ *   - mid-grid specular reflection on the axis, periodic z, free-slip or
+ *     no-slip wall at r = nr (Sec. III.A-C).
+ *
+ * Grid and layout.  The half-plane holds nz (along the axis) x nr (radial)
+ * nodes (k, j) at z_k = k + 1/2, r_j = j + 1/2; dt = dx = 1, c_s^2 = 1/3.
+ * Every host array passed through this interface is double, of length
+ * nz * nr, indexed [j * nz + k] (z contiguous).  Host arrays are copied in or
+ * out during the call and never retained.
+ *
+ * Ownership.  A handle owns all device memory of one solve (populations,
+ * auxiliary fields, scratch); lbm_axi_destroy releases it.  There is no global
+ * state apart from the optional allocator hook.  A handle is not thread-safe;
+ * different handles may be used from different threads.
+ *
+ * Errors.  Every int-returning call returns LBM_OK (0) or a negative
+ * LBM_ERR_* code; lbm_axi_strerror() names it.  After LBM_ERR_UNPHYSICAL or
+ * LBM_ERR_CUDA the populations are undefined until lbm_axi_init is called.
+ * No call aborts the process or traps on the device.
+ */
+#ifndef LBM_AXI_H
+#define LBM_AXI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = -1, /* bad size, NULL handle/pointer, out-of-range option */
+    LBM_ERR_OOM = -2,         /* device or pinned-host allocation failed */
+    LBM_ERR_CUDA = -3,        /* a CUDA runtime call or launch failed */
+    LBM_ERR_UNPHYSICAL = -4,  /* rho <= 0, psi^2 = rho/3 - P_k < 0, or a non-finite value */
+    LBM_ERR_TIMEOUT = -5,     /* a bounded device wait gave up */
+    LBM_ERR_STATE = -6        /* call out of order (e.g. step before init) */
+};
+
+/* Equation of state P_k(rho).
+ *   LBM_EOS_VDW: P_k = lambda (8 rho T / (3 - rho) - 3 rho^2), reduced units,
+ *                Eq. (kupershtokvdwpressure); T = T_over_Tc (T_c = 1).
+ *   LBM_EOS_CS:  Carnahan-Starling p = rho R T (1 + e + e^2 - e^3)/(1 - e)^3 - a rho^2,
+ *                e = b rho / 4 (not in the paper); T = T_over_Tc * T_c(a, b, R). */
+typedef enum { LBM_EOS_VDW = 0, LBM_EOS_CS = 1 } lbm_eos_kind;
+
+typedef struct {
+    int kind;         /* lbm_eos_kind */
+    double T_over_Tc; /* reduced temperature, (0, 1) for two-phase states */
+    double a, b, R;   /* CS constants (ignored for vdW) */
+    double lambda;    /* vdW pressure scale (ignored for CS) */
+} lbm_eos;
+
+enum { LBM_TOP_FREESLIP = 0, LBM_TOP_NOSLIP = 1, LBM_TOP_PERIODIC = 2 };
+
+/* The c^4 factor of F_axis (Sec. II.C): the paper replaces the lattice c_s by
+ * the thermodynamic c_k, c_k^2 = dP_k/drho at the local density. */
+enum {
+    LBM_KAPPA_THERMO = 0,  /* c_k^4 (the substitution as the paper states it; default) */
+    LBM_KAPPA_LATTICE = 1, /* c_s^4 = 1/9 (the lattice moment of the Taylor expansion) */
+    LBM_KAPPA_MIXED = 2    /* c_s^2 c_k^2 */
+};
+
+typedef struct {
+    int precision;  /* 64: FP64 populations and arithmetic; 32: FP32 populations stored as
+                       deviations f_i - w_i rho_ref, FP32 arithmetic, FP64 reductions */
+    int top_bc;     /* LBM_TOP_*: wall at r = nr; PERIODIC makes r periodic (plain 2D box) */
+    int axis_terms; /* 1: axisymmetric source h_i and F_axis; 0: plain 2D (z, r) plane */
+    int multiphase; /* 1: pseudopotential force; 0: ideal single-phase fluid */
+    int kappa_mode; /* LBM_KAPPA_* */
+    int hr_sign;    /* sign of u_r/r inside H_r: -1 (default, the viscous hoop term
+                       2 mu d_r(u_r/r)); +1 reproduces the printed formula */
+    double rho_ref; /* reference density of the FP32 deviation storage (0 allowed) */
+    double g_z;     /* constant body acceleration along z (0 in the paper's runs) */
+    void* stream;   /* cudaStream_t to run on; NULL: the handle creates its own */
+} lbm_axi_opts;
+
+typedef struct lbm_axi lbm_axi;
+
+/* Fill *opts with the defaults: FP64, free-slip top, axis terms and
+ * multiphase on, LBM_KAPPA_THERMO, hr_sign -1, rho_ref 0, g_z 0, own stream. */
+void lbm_axi_default_opts(lbm_axi_opts* opts);
+
+/* Create a solve on the current CUDA device.
+ *   nz, nr >= 1; tau > 1/2 (BGK relaxation time, nu = (tau - 1/2)/3);
+ *   eos: required when opts->multiphase (else may be NULL); A: Kupershtokh
+ *   mixing parameter (A = -0.152 recovers the vdW coexistence curve);
+ *   opts: NULL for the defaults.
+ * Allocates all device memory of the solve.  Returns LBM_ERR_INVALID_ARG for
+ * bad arguments, LBM_ERR_OOM when memory runs out. */
+int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, const lbm_axi_opts* opts,
+                   lbm_axi** out);
+
+/* Set the populations to equilibrium, f_i = f_i^eq(rho, u) (Sec. II.A), with
+ * u taken as the bare velocity sum_i c_i f_i / rho.  rho is required; u_z and
+ * u_r may be NULL (zero).  Host arrays, nz*nr doubles.  Synchronous. */
+int lbm_axi_init(lbm_axi* h, const double* rho, const double* u_z, const double* u_r);
+
+/* Same as lbm_axi_init with device arrays (nz*nr doubles, [j*nz + k]). */
+int lbm_axi_init_device(lbm_axi* h, const double* d_rho, const double* d_u_z, const double* d_u_r);
+
+/* Advance n >= 0 time steps: gather (pull streaming with the boundary rules),
+ * moments, psi, F = F_K + F_axis (+ rho g_z), EDM + BGK collision with the
+ * axisymmetric source.  Waits for the stream and returns LBM_ERR_UNPHYSICAL
+ * if any step met rho <= 0, psi^2 < 0 or a non-finite value. */
+int lbm_axi_step(lbm_axi* h, long long n);
+
+/* As lbm_axi_step, but only enqueues the work on the handle's stream; the
+ * error status of the enqueued steps is returned by the next lbm_axi_sync. */
+int lbm_axi_step_async(lbm_axi* h, long long n);
+
+/* Wait for the handle's stream; return the sticky error status of the steps
+ * enqueued since the previous sync (and clear it). */
+int lbm_axi_sync(lbm_axi* h);
+
+/* Measurement aid: advance n steps exactly like lbm_axi_step, but launch
+ * kernel by kernel (no CUDA graph) with a CUDA event pair around every launch
+ * on the handle's stream.  ms[0] receives the summed device time of the n
+ * kernel-(a) launches (gather, rho, j, psi), ms[1] that of the n kernel-(b)
+ * launches (fused force + EDM + source + collide).  Synchronous. */
+int lbm_axi_time_kernels(lbm_axi* h, long long n, double* ms);
+
+/* Macroscopic fields of the current state (host arrays, any may be NULL):
+ * rho = sum_i f_i; physical velocity u = sum_i c_i f_i / rho + F / (2 rho)
+ * (Sec. II.A); p = P_k(rho) (rho/3 for a single-phase run).  Synchronous. */
+int lbm_axi_moments(lbm_axi* h, double* rho, double* u_z, double* u_r, double* p);
+
+/* Same as lbm_axi_moments into device arrays (nz*nr doubles each, may be NULL). */
+int lbm_axi_moments_device(lbm_axi* h, double* d_rho, double* d_u_z, double* d_u_r, double* d_p);
+
+/* r-weighted mass sum_{k,j} (j + 1/2) rho(k, j) (the 2 pi of the volume
+ * element omitted) and, if mass_plain != NULL, sum rho.  FP64 reduction with a
+ * fixed summation order (bitwise reproducible).  Synchronous. */
+int lbm_axi_mass(lbm_axi* h, double* mass_rweighted, double* mass_plain);
+
+/* Young-Laplace pressure jump for a droplet centred at (z_c, r_c):
+ * dp = <P_k>_{d < r_in} - <P_k>_{d > r_out}, d the distance of node (z_k, r_j)
+ * from the centre (Sec. III.A, Eq. laplacepressure).  FP64 reduction.
+ * Returns LBM_ERR_INVALID_ARG if either region holds no node. */
+int lbm_axi_pressure_jump(lbm_axi* h, double z_c, double r_c, double r_in, double r_out, double* dp);
+
+/* Release the solve.  NULL is a no-op.  Waits for the handle's stream. */
+void lbm_axi_destroy(lbm_axi* h);
+
+/* Absolute EOS temperature T and critical temperature T_c of a created solve. */
+int lbm_axi_temperature(const lbm_axi* h, double* T, double* T_c);
+
+/* Bytes of device memory the solve holds (populations, fields, scratch). */
+int lbm_axi_device_bytes(const lbm_axi* h, size_t* bytes);
+
+/* Device memory a solve of this size and precision would hold. */
+size_t lbm_axi_footprint(int nz, int nr, int precision);
+
+/* Host-side EOS helpers (no GPU): critical temperature T_c of the EOS and the
+ * coexistence densities at eos->T_over_Tc from the Maxwell equal-area
+ * construction, integral_{v_l}^{v_v} (P_k(v) - p_s) dv = 0 with v = 1/rho. */
+int lbm_eos_critical_temperature(const lbm_eos* eos, double* T_c);
+int lbm_eos_coexistence(const lbm_eos* eos, double* rho_v, double* rho_l);
+/* P_k(rho) and dP_k/drho at the temperature of eos. */
+int lbm_eos_pressure(const lbm_eos* eos, double rho, double* p, double* dpdrho);
+
+/* Route the library's device allocations through a caller's allocator (for
+ * example a framework's caching allocator).  Process-wide; affects handles
+ * created afterwards.  Pass NULL, NULL to restore cudaMalloc/cudaFree.  alloc
+ * returns a device pointer aligned to at least 256 bytes or NULL. */
+int lbm_axi_set_allocator(void* (*alloc)(size_t bytes, void* ctx), void (*release)(void* ptr, void* ctx),
+                          void* ctx);
+
+/* Text for an LBM_* code (static storage). */
+const char* lbm_axi_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_AXI_H */

@@ -1,0 +1,37 @@
+// Host-side launchers of the kernels, one explicit instantiation per
+// precision (kernels_f32.cu, kernels_f64.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int kReduceBlocks = 304;  // 2 x 152 SMs; fixed so reductions are reproducible
+
+template <typename R>
+struct Ops {
+    // kernel (a): gather, rho/j, psi; raises bits in *err.
+    static cudaError_t density(const Params<R>& p, const R* f, R* aux, int* err, cudaStream_t s);
+    // kernel (b): the fused stream + force + EDM + axisymmetric source + collide step.
+    static cudaError_t update(const Params<R>& p, const Params<double>& pd, const R* f, R* fout, const R* aux,
+                              cudaStream_t s);
+    // rho, physical u, P_k of the current state into mout[4][nz*nr] (after density()).
+    static cudaError_t moments(const Params<R>& p, const Params<double>& pd, const R* f, const R* aux,
+                               double* mout, cudaStream_t s);
+    static cudaError_t init(const Params<R>& p, double rho_ref, const double* rho, const double* uz,
+                            const double* ur, R* f, cudaStream_t s);
+    // kernel (c): out[0] = sum (j+1/2) rho, out[1] = sum rho.
+    static cudaError_t mass(const Params<R>& p, double rho_ref, const R* aux, double* partial, double* out,
+                            cudaStream_t s);
+    // out[0..3] = sum P_k inside, count inside, sum P_k outside, count outside.
+    static cudaError_t pjump(const Params<R>& p, const Params<double>& pd, const R* aux, double zc, double rc,
+                             double rin, double rout, double* partial, double* out, cudaStream_t s);
+    // dynamic shared memory of one k_update CTA, bytes
+    static size_t update_smem();
+    // one-time kernel attributes (shared-memory opt-in); call outside stream capture
+    static cudaError_t prepare();
+};
+
+}  // namespace lbm

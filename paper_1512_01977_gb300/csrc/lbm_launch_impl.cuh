@@ -1,0 +1,96 @@
+// Definitions of Ops<R>; included once per precision.
+#pragma once
+
+#include "lbm_kernels.cuh"
+#include "lbm_launch.h"
+
+namespace lbm {
+
+// Tile of kernel (b) per precision: TZ nodes along z (coalesced) x TR rows.
+template <typename R>
+struct UpdateTile;
+template <>
+struct UpdateTile<float> {
+    static constexpr int TZ = 32, TR = 16;
+};
+template <>
+struct UpdateTile<double> {
+    static constexpr int TZ = 32, TR = 8;
+};
+
+template <typename R>
+size_t Ops<R>::update_smem() {
+    using T = UpdateTile<R>;
+    return sizeof(R) * (size_t)TileShape<T::TZ, T::TR>::elems;
+}
+
+template <typename R>
+static cudaError_t launch_update(const Params<R>& p, const Params<double>& pd, const R* f, R* fout, const R* aux,
+                                 double* mout, bool moments, cudaStream_t s) {
+    using T = UpdateTile<R>;
+    const size_t smem = Ops<R>::update_smem();
+    dim3 grid((p.nz + T::TZ - 1) / T::TZ, (p.nr + T::TR - 1) / T::TR);
+    if (moments) {
+        k_update<R, T::TZ, T::TR, true><<<grid, 256, smem, s>>>(p, pd, f, nullptr, aux, mout);
+    } else {
+        k_update<R, T::TZ, T::TR, false><<<grid, 256, smem, s>>>(p, pd, f, fout, aux, nullptr);
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Ops<R>::prepare() {
+    using T = UpdateTile<R>;
+    const int smem = (int)update_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_update<R, T::TZ, T::TR, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_update<R, T::TZ, T::TR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+    return e;
+}
+
+template <typename R>
+cudaError_t Ops<R>::density(const Params<R>& p, const R* f, R* aux, int* err, cudaStream_t s) {
+    dim3 block(32, 8), grid((p.nz + 31) / 32, (p.nr + 7) / 8);
+    k_density<R><<<grid, block, 0, s>>>(p, f, aux, err);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Ops<R>::update(const Params<R>& p, const Params<double>& pd, const R* f, R* fout, const R* aux,
+                           cudaStream_t s) {
+    return launch_update<R>(p, pd, f, fout, aux, nullptr, false, s);
+}
+
+template <typename R>
+cudaError_t Ops<R>::moments(const Params<R>& p, const Params<double>& pd, const R* f, const R* aux, double* mout,
+                            cudaStream_t s) {
+    return launch_update<R>(p, pd, f, nullptr, aux, mout, true, s);
+}
+
+template <typename R>
+cudaError_t Ops<R>::init(const Params<R>& p, double rho_ref, const double* rho, const double* uz, const double* ur,
+                         R* f, cudaStream_t s) {
+    dim3 block(32, 8), grid((p.nz + 31) / 32, (p.nr + 7) / 8);
+    k_init<R><<<grid, block, 0, s>>>(p, rho_ref, rho, uz, ur, f);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Ops<R>::mass(const Params<R>& p, double rho_ref, const R* aux, double* partial, double* out,
+                         cudaStream_t s) {
+    k_mass<R><<<kReduceBlocks, 256, 0, s>>>(p, rho_ref, aux, partial);
+    k_reduce_final<2><<<1, 32, 0, s>>>(partial, kReduceBlocks, out);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Ops<R>::pjump(const Params<R>& p, const Params<double>& pd, const R* aux, double zc, double rc,
+                          double rin, double rout, double* partial, double* out, cudaStream_t s) {
+    k_pjump<R><<<kReduceBlocks, 256, 0, s>>>(p, pd, aux, zc, rc, rin, rout, partial);
+    k_reduce_final<4><<<1, 32, 0, s>>>(partial, kReduceBlocks, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

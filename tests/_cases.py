@@ -1,0 +1,62 @@
+"""Test cases expressed once and turned into both an oracle solve and a CUDA
+solve with the same numbers.  Inputs come from paper_1512_01977_gb300.inputs;
+coexistence densities for initial states come from the oracle."""
+import dataclasses
+
+import numpy as np
+
+import oracle as O
+
+
+@dataclasses.dataclass
+class Case:
+    nz: int
+    nr: int
+    tau: float = 1.0
+    eos: int = O.EOS_CS
+    T_over_Tc: float = 0.8
+    A: float = -0.152
+    lam: float = 0.01
+    top: int = O.TOP_FREESLIP
+    axis: int = 1
+    multiphase: int = 1
+    kappa: int = O.KAPPA_THERMO
+    hr_sign: int = -1
+    gz: float = 0.0
+
+    def oracle_params(self):
+        p = O.Params(nz=self.nz, nr=self.nr, tau=self.tau, A=self.A, eos=self.eos, lam=self.lam, top=self.top,
+                     axis=self.axis, multiphase=self.multiphase, kappa=self.kappa, hr_sign=self.hr_sign,
+                     gz=self.gz)
+        Tc, _ = O.eos.critical_point(p)
+        return p.replace(T=self.T_over_Tc * Tc)
+
+    def coexistence(self):
+        return O.eos.maxwell_densities(self.oracle_params())
+
+    def solver(self, precision=64, rho_ref=0.0):
+        from paper_1512_01977_gb300 import lbm
+
+        eos = lbm.make_eos(self.eos, self.T_over_Tc, lam=self.lam) if self.multiphase else None
+        return lbm.Solver(self.nz, self.nr, self.tau, eos=eos, A=self.A, precision=precision, top=self.top,
+                          axis=self.axis, multiphase=self.multiphase, kappa=self.kappa, hr_sign=self.hr_sign,
+                          rho_ref=rho_ref, g_z=self.gz)
+
+
+def run_oracle(case, fields, steps):
+    o = O.Oracle(case.oracle_params()).init(*fields)
+    o.step(steps)
+    return o
+
+
+def run_gpu(case, fields, steps, precision=64, rho_ref=0.0):
+    s = case.solver(precision, rho_ref)
+    s.init(*fields)
+    s.step(steps)
+    return s
+
+
+def rel_err(a, b):
+    """max |a - b| / max |b| (b the reference)."""
+    scale = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0))

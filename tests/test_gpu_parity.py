@@ -1,0 +1,222 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+FP64 bar: max |gpu - oracle| / max |oracle| <= 1e-12 for rho, u_z, u_r and
+P_k after the stated steps (rounding order differs between the two, nothing
+else).  FP32 bars are per result and derived in the FP32 tests below.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1512_01977_gb300 import inputs as I
+from tests._cases import Case, rel_err, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_01977_gb300 import build, lbm
+
+    build.build()
+    lbm.lib()
+
+
+def _droplet_fields(case, R, du=0.0, seed=0, eps=0.0):
+    rv, rl = case.coexistence()
+    rho, uz, ur = I.droplet(case.nz, case.nr, R, rl, rv, eps=eps)
+    if du:
+        _, vz, vr = I.random_state(case.nz, case.nr, 1.0, 0.0, du, seed)
+        uz, ur = vz, vr * (np.arange(case.nr) + 0.5)[:, None] / case.nr  # u_r -> 0 at the axis
+    return rho, uz, ur
+
+
+def _compare(case, fields, steps, tol=TOL64):
+    o = run_oracle(case, fields, steps)
+    s = run_gpu(case, fields, steps)
+    mo, mg = o.moments(), s.moments()
+    errs = {k: rel_err(mg[k], mo[k]) for k in ("rho", "uz", "ur", "p")}
+    s.close()
+    for k, e in errs.items():
+        assert e <= tol, (k, errs)
+    return errs
+
+
+def test_init_moments_roundtrip():
+    """f = f^eq(rho, u) then moments: rho back exactly, u = u0 + F/(2 rho)."""
+    c = Case(40, 24)
+    fields = _droplet_fields(c, 9, du=1e-3)
+    o = O.Oracle(c.oracle_params()).init(*fields)
+    s = c.solver().init(*fields)
+    mg, mo = s.moments(), o.moments()
+    np.testing.assert_allclose(mg["rho"], fields[0], rtol=1e-15, atol=0)
+    for k in ("rho", "uz", "ur", "p"):
+        assert rel_err(mg[k], mo[k]) <= 1e-14, k
+    s.close()
+
+
+def test_droplet_fp64_ragged_tiles():
+    """Droplet with a random velocity field on a grid that is not a multiple
+    of the tile in either direction (ragged last tiles)."""
+    c = Case(45, 27)
+    _compare(c, _droplet_fields(c, 10, du=2e-3, seed=1), 150)
+
+
+@pytest.mark.parametrize("top", [O.TOP_FREESLIP, O.TOP_NOSLIP, O.TOP_PERIODIC])
+def test_boundaries_fp64(top):
+    c = Case(36, 20, top=top, axis=0 if top == O.TOP_PERIODIC else 1)
+    _compare(c, _droplet_fields(c, 8, du=2e-3, seed=2), 60)
+
+
+@pytest.mark.parametrize("kappa", [O.KAPPA_THERMO, O.KAPPA_LATTICE, O.KAPPA_MIXED])
+def test_kappa_modes_fp64(kappa):
+    c = Case(40, 24, kappa=kappa)
+    _compare(c, _droplet_fields(c, 9, du=1e-3, seed=3), 60)
+
+
+def test_vdw_fp64():
+    c = Case(48, 28, tau=1.5, eos=O.EOS_VDW, A=0.0, T_over_Tc=0.8)
+    _compare(c, _droplet_fields(c, 10, du=1e-3, seed=4), 60)
+
+
+def test_printed_hr_sign_fp64():
+    """The +u_r/r reading of H_r is selectable and matches the oracle's."""
+    c = Case(40, 24, hr_sign=+1)
+    _compare(c, _droplet_fields(c, 9, du=1e-3, seed=5), 20)
+
+
+def test_single_phase_body_force_fp64():
+    c = Case(8, 16, multiphase=0, top=O.TOP_NOSLIP, gz=1e-5)
+    rho, uz, ur = I.random_state(8, 16, 1.0, 0.01, 1e-3, 6)
+    _compare(c, (rho, uz, ur), 200)
+
+
+@pytest.mark.parametrize("nz,nr", [(1, 1), (1, 7), (5, 1), (3, 3), (33, 9), (31, 17)])
+def test_tiny_and_thin_grids_fp64(nz, nr):
+    """Grids thinner than the stencil halo (multiple reflections, wraps)."""
+    c = Case(nz, nr, multiphase=1, T_over_Tc=0.9)
+    rho, uz, ur = I.random_state(nz, nr, 0.2, 0.01, 1e-3, nz * 100 + nr)
+    _compare(c, (rho, uz, ur), 30)
+
+
+def test_radial_wave_channel_fp64():
+    """The paper's 1 x N_r wave channel (nz = 1), vdW, no-slip top."""
+    c = Case(1, 400, tau=0.6, eos=O.EOS_VDW, A=0.0, T_over_Tc=0.8, top=O.TOP_NOSLIP)
+    fields = I.radial_bump(1, 400, 1.8, 1.8e-3, 10.0)
+    _compare(c, fields, 300)
+
+
+def test_c1_droplet_full_fp64():
+    """64 x 64 droplet (CS, T = 0.8 Tc, A = -0.152, tau = 1, R = 16, tanh width 2),
+    the full 2000 steps."""
+    c = Case(64, 64)
+    errs = _compare(c, _droplet_fields(c, 16), 2000)
+    print("C1 parity", errs)
+
+
+def test_mass_and_pressure_jump_fp64():
+    c = Case(64, 40)
+    fields = _droplet_fields(c, 12)
+    o = run_oracle(c, fields, 100)
+    s = run_gpu(c, fields, 100)
+    mr, m = s.mass()
+    assert mr == pytest.approx(o.mass_rweighted(), rel=1e-13)
+    assert m == pytest.approx(o.mass(), rel=1e-13)
+    mo = o.moments()
+    Z, Rr = I.grid(64, 40)
+    d = np.sqrt((Z - 32) ** 2 + Rr**2)
+    dp_o = mo["p"][d < 6].mean() - mo["p"][d > 20].mean()
+    assert s.pressure_jump(32.0, 0.0, 6.0, 20.0) == pytest.approx(dp_o, rel=1e-12)
+    s.close()
+
+
+def test_step_chunking_is_invisible():
+    """n steps in one call (CUDA-graph chunks + tail) equal n single-step calls."""
+    c = Case(40, 24)
+    fields = _droplet_fields(c, 9, du=1e-3)
+    a = run_gpu(c, fields, 301)
+    b = c.solver().init(*fields)
+    for _ in range(301):
+        b.step(1)
+    ma, mb = a.moments(), b.moments()
+    for k in ma:
+        np.testing.assert_array_equal(ma[k], mb[k])
+    a.close()
+    b.close()
+
+
+def test_unphysical_state_is_reported():
+    from paper_1512_01977_gb300 import lbm
+
+    c = Case(16, 8)
+    rho = np.full((8, 16), 0.2)
+    rho[3, 5] = -0.1
+    s = c.solver().init(rho)
+    with pytest.raises(lbm.LbmError) as e:
+        s.step(5)
+    assert e.value.code == lbm.ERR_UNPHYSICAL
+    s.init(np.full((8, 16), 0.2))  # recoverable: re-init and continue
+    s.step(5)
+    s.close()
+
+
+def test_invalid_calls():
+    from paper_1512_01977_gb300 import lbm
+
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(0, 4, 1.0, eos=lbm.make_eos())
+    with pytest.raises(lbm.LbmError):
+        lbm.Solver(4, 4, 0.4, eos=lbm.make_eos())
+    s = lbm.Solver(4, 4, 1.0, eos=lbm.make_eos())
+    with pytest.raises(lbm.LbmError) as e:
+        s.step(1)
+    assert e.value.code == lbm.ERR_STATE
+    s.close()
+
+
+def test_torch_allocator_and_stream():
+    import torch
+
+    from paper_1512_01977_gb300 import lbm
+
+    c = Case(40, 24)
+    fields = _droplet_fields(c, 9, du=1e-3)
+    ref = run_gpu(c, fields, 50).moments()
+    lbm.use_torch_allocator()
+    try:
+        st = torch.cuda.Stream()
+        eos = lbm.make_eos(c.eos, c.T_over_Tc)
+        s = lbm.Solver(c.nz, c.nr, c.tau, eos=eos, A=c.A, stream=st.cuda_stream)
+        s.init(*fields).step(50)
+        m = s.moments()
+        s.close()
+    finally:
+        lbm.use_cuda_allocator()
+    for k in ref:
+        np.testing.assert_array_equal(m[k], ref[k])
+
+
+def test_device_init_and_moments():
+    import torch
+
+    from paper_1512_01977_gb300 import lbm
+
+    c = Case(40, 24)
+    fields = _droplet_fields(c, 9, du=1e-3)
+    host = run_gpu(c, fields, 40).moments()
+    s = c.solver()
+    d = [torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda") for a in fields]
+    lbm.lbm_axi_init_device(s.h, *d)
+    s.step(40)
+    out = [torch.empty(24 * 40, dtype=torch.float64, device="cuda") for _ in range(4)]
+    lbm.lbm_axi_moments_device(s.h, *out)
+    torch.cuda.synchronize()
+    for k, t in zip(("rho", "uz", "ur", "p"), out):
+        np.testing.assert_array_equal(t.cpu().numpy().reshape(24, 40), host[k])
+    s.close()
