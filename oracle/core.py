@@ -23,6 +23,7 @@ class _CParams(C.Structure):
         ("eos", C.c_int), ("T", C.c_double), ("a", C.c_double), ("b", C.c_double),
         ("R", C.c_double), ("lam", C.c_double), ("top", C.c_int), ("axis", C.c_int),
         ("multiphase", C.c_int), ("kappa", C.c_int), ("hr_sign", C.c_int), ("gz", C.c_double),
+        ("r0", C.c_double),
     ]
 
 
@@ -46,6 +47,7 @@ class Params:
     kappa: int = KAPPA_THERMO
     hr_sign: int = -1
     gz: float = 0.0
+    r0: float = 0.0
 
     def replace(self, **kw):
         return dataclasses.replace(self, **kw)

@@ -52,6 +52,8 @@ typedef struct {
     int kappa;      /* which c^4 multiplies F_axis: ORC_KAPPA_THERMO (c_k^4) or _LATTICE (c_s^4) */
     int hr_sign;    /* sign in front of u_r/r inside H_r */
     double gz;      /* constant body acceleration along z (0 for the paper's runs) */
+    double r0;      /* row j sits at r = r0 + j + 1/2; 0 for a lattice that starts at the
+                       axis.  r0 > 0 describes a window cut out of a larger lattice (tests). */
 } orc_params;
 
 /* ------------------------------------------------------------------ EOS -- */
@@ -366,7 +368,7 @@ static int orc_fields(const orc_params* P, const double* f, orc_work* w) {
         orc_grad(P, w->psiz, w->Hr, w->psirz);
     }
     for (int j = 0; j < P->nr; j++) {
-        double r = j + 0.5;
+        double r = P->r0 + j + 0.5;
         for (int k = 0; k < P->nz; k++) {
             long e = orc_ext(P, k, j);
             double rho = w->rho[e];
@@ -398,7 +400,7 @@ static int orc_fields(const orc_params* P, const double* f, orc_work* w) {
         orc_grad(P, w->ur, w->durdz, w->durdr);
         double nu = (P->tau - 0.5) / 3.0;
         for (int j = 0; j < P->nr; j++) {
-            double r = j + 0.5;
+            double r = P->r0 + j + 0.5;
             for (int k = 0; k < P->nz; k++) {
                 long e = orc_ext(P, k, j);
                 double rho = w->rho[e];
@@ -415,7 +417,7 @@ static int orc_fields(const orc_params* P, const double* f, orc_work* w) {
 static void orc_collide(const orc_params* P, const double* f, orc_work* w) {
     long n = (long)P->nz * P->nr;
     for (int j = 0; j < P->nr; j++) {
-        double r = j + 0.5;
+        double r = P->r0 + j + 0.5;
         for (int k = 0; k < P->nz; k++) {
             long e = orc_ext(P, k, j);
             double rho = w->rho[e];

@@ -23,11 +23,12 @@ class Case:
     kappa: int = O.KAPPA_THERMO
     hr_sign: int = -1
     gz: float = 0.0
+    r0: float = 0.0  # oracle only: radial offset of a window cut from a larger lattice
 
     def oracle_params(self):
         p = O.Params(nz=self.nz, nr=self.nr, tau=self.tau, A=self.A, eos=self.eos, lam=self.lam, top=self.top,
                      axis=self.axis, multiphase=self.multiphase, kappa=self.kappa, hr_sign=self.hr_sign,
-                     gz=self.gz)
+                     gz=self.gz, r0=self.r0)
         Tc, _ = O.eos.critical_point(p)
         return p.replace(T=self.T_over_Tc * Tc)
 
@@ -60,3 +61,17 @@ def rel_err(a, b):
     """max |a - b| / max |b| (b the reference)."""
     scale = np.max(np.abs(b))
     return float(np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0))
+
+
+U_FLOOR = 1e-3  # lattice velocity scale below which velocity errors are measured absolutely
+
+
+def vel_err(mg, mo):
+    """max |u_gpu - u_oracle| (both components) / max(max |u_oracle|, U_FLOOR).
+
+    Velocities are compared as a vector against their own scale; the floor
+    keeps states whose velocity has decayed to round-off (or is zero by
+    symmetry) from turning rounding noise into a large relative error."""
+    du = max(np.max(np.abs(mg["uz"] - mo["uz"])), np.max(np.abs(mg["ur"] - mo["ur"])))
+    umax = np.max(np.hypot(mo["uz"], mo["ur"]))
+    return float(du / max(umax, U_FLOOR))
