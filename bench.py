@@ -31,8 +31,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 NZ, NR, TAU, A, T_OVER_TC = 4096, 2048, 0.6, -0.152, 0.9
-BYTES_A = 52  # kernel (a), FP32: 9 x 4 B population reads + 4 x 4 B field writes per node
-BYTES_B = 88  # kernel (b), FP32: 9 x 4 B reads + 4 x 4 B field reads + 9 x 4 B writes per node
+BYTES_FUSED = 72  # fused step kernel, FP32: 9 x 4 B population reads + 9 x 4 B writes per node
+BYTES_A = 52  # split path kernel (a), FP32: 9 x 4 B population reads + 4 x 4 B field writes per node
+BYTES_B = 88  # split path kernel (b), FP32: 9 x 4 B reads + 4 x 4 B field reads + 9 x 4 B writes per node
 WORKLOAD = "density wave 4096x2048, CS T=0.9Tc, tau=0.6, A=-0.152, FP32 deviation storage"
 
 
@@ -260,11 +261,13 @@ def run_ours(args):
     value = ws * n * args.steps / (ms_max * 1e3)  # MLUPS
 
     # ---- per-kernel device time (CUDA events around each launch, same stream)
+    path, rows_per_cta = lbm.lbm_axi_get_tuning(s.h)
     kr = max(20, min(args.steps, 1000))
     ms_a, ms_b = lbm.lbm_axi_time_kernels(s.h, kr)
     t_a, t_b = ms_a / kr * 1e-3, ms_b / kr * 1e-3
     peak, peak_kind = _peaks()
-    ach_b = BYTES_B * n / t_b / 1e9
+    bytes_main = BYTES_FUSED if path == lbm.PATH_FUSED else BYTES_B
+    ach_b = bytes_main * n / t_b / 1e9
     traffic = _ncu_traffic()
 
     # ---- end to end through the C ABI: pinned host -> init -> K steps -> moments -> pinned host
@@ -297,17 +300,18 @@ def run_ours(args):
                        "l2": "no flush: inputs larger than L2 (2 x 302 MB FP32 population buffers)",
                        "parallelism": "replicas only (independent solves per GPU)",
                        "device": props.name},
-            "roofline": {"bound": "hbm", "kernel": "k_update (fused force+EDM+source+collide)",
+            "roofline": {"bound": "hbm",
+                         "kernel": "k_step (one-pass gather+psi+forces+EDM+source+collide)" if path == lbm.PATH_FUSED
+                         else "k_update (forces+EDM+source+collide)",
                          "achieved": ach_b, "peak": peak, "unit": "GB/s", "frac": ach_b / peak,
                          "peak_source": peak_kind, "traffic": traffic,
-                         "algorithmic_bytes_per_node": BYTES_B, "avg_launch_us": t_b * 1e6,
-                         "kernel_a_avg_launch_us": t_a * 1e6,
-                         "kernel_a_frac": BYTES_A * n / t_a / 1e9 / peak,
-                         "step_frac": (BYTES_A + BYTES_B) * n / (t_a + t_b) / 1e9 / peak},
+                         "algorithmic_bytes_per_node": bytes_main, "avg_launch_us": t_b * 1e6,
+                         "rows_per_cta": rows_per_cta,
+                         "vs_140B_split_design_frac": 140 * n / (t_a + t_b) / 1e9 / peak},
             "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": 3 * 8 * n / args.steps,
                     "d2h_bytes_per_step": 4 * 8 * n / args.steps,
                     "note": "one solve: init from pinned host fields, K steps, moments back to pinned host"},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (1 if path == lbm.PATH_FUSED else 2) * args.steps,
             "clocks": clk.summary(),
             "mass_rweighted": mass_rw,
         }

@@ -128,10 +128,29 @@ int lbm_axi_sync(lbm_axi* h);
 
 /* Measurement aid: advance n steps exactly like lbm_axi_step, but launch
  * kernel by kernel (no CUDA graph) with a CUDA event pair around every launch
- * on the handle's stream.  ms[0] receives the summed device time of the n
- * kernel-(a) launches (gather, rho, j, psi), ms[1] that of the n kernel-(b)
- * launches (fused force + EDM + source + collide).  Synchronous. */
+ * on the handle's stream.  ms[1] receives the summed device time of the n
+ * launches of the step's main kernel (the fused step kernel, or kernel (b) of
+ * the split path); ms[0] that of the n kernel-(a) launches of the split path
+ * (0 on the fused path).  Synchronous. */
 int lbm_axi_time_kernels(lbm_axi* h, long long n, double* ms);
+
+/* Kernel configuration of a solve (performance only).
+ *   path: LBM_PATH_FUSED -- one kernel per step (gather, moments, psi, forces,
+ *         collision in a single pass over the populations, 72 B per node in FP32);
+ *         needs nr >= 16.  LBM_PATH_SPLIT -- kernel (a) (gather, rho, j, psi into
+ *         field planes) then kernel (b) (forces + collision), 140 B per node.
+ *   rows_per_cta: rows of each 64-wide z-strip one CTA of the fused kernel marches
+ *         over (>= 4).
+ * The default is FUSED when nr >= 16 with rows_per_cta chosen for about two
+ * waves of CTAs.  The two paths agree to rounding.  Setting waits for the
+ * handle's stream. */
+enum { LBM_PATH_FUSED = 1, LBM_PATH_SPLIT = 2 };
+typedef struct {
+    int path;
+    int rows_per_cta;
+} lbm_axi_tuning;
+int lbm_axi_get_tuning(const lbm_axi* h, lbm_axi_tuning* t);
+int lbm_axi_set_tuning(lbm_axi* h, const lbm_axi_tuning* t);
 
 /* Macroscopic fields of the current state (host arrays, any may be NULL):
  * rho = sum_i f_i; physical velocity u = sum_i c_i f_i / rho + F / (2 rho)

@@ -3,7 +3,7 @@
 // the absolute temperature of a solve and to build two-phase initial states.
 #include <math.h>
 
-#include "../../include/lbm_axi.h"
+#include "lbm_axi.h"
 #include "lbm_eos_host.h"
 
 namespace lbm {

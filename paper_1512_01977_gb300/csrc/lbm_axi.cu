@@ -6,7 +6,7 @@
 
 #include <new>
 
-#include "../../include/lbm_axi.h"
+#include "lbm_axi.h"
 #include "lbm_eos_host.h"
 #include "lbm_launch.h"
 
@@ -63,6 +63,8 @@ struct lbm_axi {
     bool initialized;
     int pending;  // error status carried to the next sync
     size_t bytes;
+    int path;          // LBM_PATH_FUSED or LBM_PATH_SPLIT
+    int rows_per_cta;  // rows of a z-strip per CTA of the fused kernel
     Params<float> pf;
     Params<double> pdd;
 };
@@ -109,10 +111,31 @@ double stored_rho_ref(const lbm_axi* h) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
 
-// One step: kernel (a) on the current populations, kernel (b) into the other buffer.
+// Default rows per CTA of the fused kernel: about two waves of four CTAs per SM.
+int default_rows_per_cta(int nz, int nr, int strip) {
+    const long long strips = (nz + strip - 1) / strip;
+    long long rows = (nr * strips + 1215) / 1216;
+    rows = (rows + 3) / 4 * 4;
+    if (rows < 16) rows = 16;
+    if (rows > 512) rows = 512;
+    return (int)rows;
+}
+
+// One step.  Fused path: kernel (b') reads f[cur] and writes f[cur^1].  Split
+// path: kernel (a) on the current populations, kernel (b) into the other buffer.
 cudaError_t enqueue_step(lbm_axi* h) {
     const int c = h->cur;
     cudaError_t e;
+    if (h->path == LBM_PATH_FUSED) {
+        if (h->precision == 32)
+            e = Ops<float>::step(h->pf, (const float*)h->f[c], (float*)h->f[c ^ 1], h->rows_per_cta, h->derr,
+                                 h->stream);
+        else
+            e = Ops<double>::step(h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1], h->rows_per_cta, h->derr,
+                                  h->stream);
+        h->cur = c ^ 1;
+        return e;
+    }
     if (h->precision == 32) {
         e = Ops<float>::density(h->pf, (const float*)h->f[c], (float*)h->aux, h->derr, h->stream);
         if (e == cudaSuccess)
@@ -310,6 +333,9 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     }
     h->pf = make_params<float>(h);
     h->pdd = make_params<double>(h);
+    h->path = nr >= lbm::kStepMinRows ? LBM_PATH_FUSED : LBM_PATH_SPLIT;
+    h->rows_per_cta = default_rows_per_cta(nz, nr, h->precision == 32 ? Ops<float>::step_strip()
+                                                                       : Ops<double>::step_strip());
     if (h->precision == 32) h->pdd = make_params_out(h);
     *h->herr = 0;
     cudaError_t err = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
@@ -418,9 +444,12 @@ int lbm_axi_time_kernels(lbm_axi* h, long long n, double* ms) {
     for (long long s = 0; s < n && e == cudaSuccess; s++) {
         const int c = h->cur;
         e = cudaEventRecord(ev[0], h->stream);
-        if (e == cudaSuccess) e = enqueue_density(h);
+        if (e == cudaSuccess && h->path == LBM_PATH_SPLIT) e = enqueue_density(h);
         if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
-        if (e == cudaSuccess) {
+        if (e == cudaSuccess && h->path == LBM_PATH_FUSED) {
+            e = enqueue_step(h);
+            h->cur = c;
+        } else if (e == cudaSuccess) {
             if (h->precision == 32)
                 e = Ops<float>::update(h->pf, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1],
                                        (const float*)h->aux, h->stream);
@@ -519,6 +548,29 @@ void lbm_axi_destroy(lbm_axi* h) {
     cudaStreamSynchronize(h->stream);
     release_all(h);
     delete h;
+}
+
+int lbm_axi_get_tuning(const lbm_axi* h, lbm_axi_tuning* t) {
+    if (!h || !t) return LBM_ERR_INVALID_ARG;
+    t->path = h->path;
+    t->rows_per_cta = h->rows_per_cta;
+    return LBM_OK;
+}
+
+int lbm_axi_set_tuning(lbm_axi* h, const lbm_axi_tuning* t) {
+    if (!h || !t) return LBM_ERR_INVALID_ARG;
+    if (t->path != LBM_PATH_FUSED && t->path != LBM_PATH_SPLIT) return LBM_ERR_INVALID_ARG;
+    if (t->path == LBM_PATH_FUSED && h->nr < lbm::kStepMinRows) return LBM_ERR_INVALID_ARG;
+    if (t->rows_per_cta < 4 || t->rows_per_cta > (1 << 20)) return LBM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ERR_CUDA;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->path = t->path;
+    h->rows_per_cta = t->rows_per_cta;
+    return LBM_OK;
 }
 
 int lbm_axi_temperature(const lbm_axi* h, double* T, double* Tc) {

@@ -1,7 +1,7 @@
 // Host EOS helpers of the library (eos_host.cu).
 #pragma once
 
-#include "../../include/lbm_axi.h"
+#include "lbm_axi.h"
 
 namespace lbm {
 bool critical_point(const lbm_eos& e, double* Tc, double* rho_c);

@@ -9,6 +9,7 @@
 namespace lbm {
 
 constexpr int kReduceBlocks = 304;  // 2 x 152 SMs; fixed so reductions are reproducible
+constexpr int kStepMinRows = 16;    // the single-pass kernel needs single reflections at the walls
 
 template <typename R>
 struct Ops {
@@ -32,6 +33,11 @@ struct Ops {
     static size_t update_smem();
     // one-time kernel attributes (shared-memory opt-in); call outside stream capture
     static cudaError_t prepare();
+    // kernel (b'): the whole step in one pass (needs nr >= kStepMinRows); rows_per_cta
+    // rows of each z-strip per CTA.
+    static cudaError_t step(const Params<R>& p, const R* f, R* fout, int rows_per_cta, int* err, cudaStream_t s);
+    static size_t step_smem();
+    static int step_strip();  // z-columns per CTA of the single-pass kernel
 };
 
 }  // namespace lbm

@@ -3,6 +3,7 @@
 
 #include "lbm_kernels.cuh"
 #include "lbm_launch.h"
+#include "lbm_step.cuh"
 
 namespace lbm {
 
@@ -38,6 +39,28 @@ static cudaError_t launch_update(const Params<R>& p, const Params<double>& pd, c
     return cudaGetLastError();
 }
 
+// Strip width and rows per iteration of the fused kernel per precision.
+template <typename R>
+struct StepTile;
+template <>
+struct StepTile<float> {
+    static constexpr int TZ = 128, RR = 2, MINB = 3;  // 288 threads, 68.6 KB of rings
+};
+template <>
+struct StepTile<double> {
+    static constexpr int TZ = 64, RR = 2, MINB = 2;  // 160 threads, 71.7 KB of rings
+};
+
+template <typename R>
+size_t Ops<R>::step_smem() {
+    return sizeof(R) * (size_t)StepShape<StepTile<R>::TZ, StepTile<R>::RR>::elems;
+}
+
+template <typename R>
+int Ops<R>::step_strip() {
+    return StepTile<R>::TZ;
+}
+
 template <typename R>
 cudaError_t Ops<R>::prepare() {
     using T = UpdateTile<R>;
@@ -47,7 +70,19 @@ cudaError_t Ops<R>::prepare() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_update<R, T::TZ, T::TR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step<R, StepTile<R>::TZ, StepTile<R>::RR, StepTile<R>::MINB>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem());
     return e;
+}
+
+template <typename R>
+cudaError_t Ops<R>::step(const Params<R>& p, const R* f, R* fout, int rows_per_cta, int* err, cudaStream_t s) {
+    if (rows_per_cta < 1) rows_per_cta = 1;
+    constexpr int TZ = StepTile<R>::TZ, RR = StepTile<R>::RR, MINB = StepTile<R>::MINB;
+    dim3 grid((p.nz + TZ - 1) / TZ, (p.nr + rows_per_cta - 1) / rows_per_cta);
+    k_step<R, TZ, RR, MINB><<<grid, StepShape<TZ, RR>::NT, step_smem(), s>>>(p, f, fout, rows_per_cta, err);
+    return cudaGetLastError();
 }
 
 template <typename R>

@@ -30,6 +30,13 @@ class lbm_axi_opts(C.Structure):
                 ("stream", C.c_void_p)]
 
 
+PATH_FUSED, PATH_SPLIT = 1, 2
+
+
+class lbm_axi_tuning(C.Structure):
+    _fields_ = [("path", C.c_int), ("rows_per_cta", C.c_int)]
+
+
 class LbmError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -59,6 +66,8 @@ _SIGS = {
     "lbm_axi_pressure_jump": (C.c_int, [_H, C.c_double, C.c_double, C.c_double, C.c_double, _D]),
     "lbm_axi_destroy": (None, [_H]),
     "lbm_axi_temperature": (C.c_int, [_H, _D, _D]),
+    "lbm_axi_get_tuning": (C.c_int, [_H, C.POINTER(lbm_axi_tuning)]),
+    "lbm_axi_set_tuning": (C.c_int, [_H, C.POINTER(lbm_axi_tuning)]),
     "lbm_axi_device_bytes": (C.c_int, [_H, C.POINTER(C.c_size_t)]),
     "lbm_axi_footprint": (C.c_size_t, [C.c_int, C.c_int, C.c_int]),
     "lbm_eos_critical_temperature": (C.c_int, [C.POINTER(lbm_eos), _D]),
@@ -208,6 +217,17 @@ def lbm_axi_temperature(h):
     T, Tc = C.c_double(), C.c_double()
     _check(lib().lbm_axi_temperature(h, C.byref(T), C.byref(Tc)), "lbm_axi_temperature")
     return T.value, Tc.value
+
+
+def lbm_axi_get_tuning(h):
+    t = lbm_axi_tuning()
+    _check(lib().lbm_axi_get_tuning(h, C.byref(t)), "lbm_axi_get_tuning")
+    return t.path, t.rows_per_cta
+
+
+def lbm_axi_set_tuning(h, path, rows_per_cta):
+    t = lbm_axi_tuning(path, rows_per_cta)
+    _check(lib().lbm_axi_set_tuning(h, C.byref(t)), "lbm_axi_set_tuning")
 
 
 def lbm_axi_device_bytes(h):

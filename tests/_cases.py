@@ -50,8 +50,12 @@ def run_oracle(case, fields, steps):
     return o
 
 
-def run_gpu(case, fields, steps, precision=64, rho_ref=0.0):
+def run_gpu(case, fields, steps, precision=64, rho_ref=0.0, tuning=None):
     s = case.solver(precision, rho_ref)
+    if tuning is not None:
+        from paper_1512_01977_gb300 import lbm
+
+        lbm.lbm_axi_set_tuning(s.h, *tuning)
     s.init(*fields)
     s.step(steps)
     return s

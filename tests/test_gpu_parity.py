@@ -40,9 +40,9 @@ def _droplet_fields(case, R, du=0.0, seed=0, eps=0.0):
     return rho, uz, ur
 
 
-def _compare(case, fields, steps, tol=TOL64):
+def _compare(case, fields, steps, tol=TOL64, tuning=None):
     o = run_oracle(case, fields, steps)
-    s = run_gpu(case, fields, steps)
+    s = run_gpu(case, fields, steps, tuning=tuning)
     mo, mg = o.moments(), s.moments()
     errs = {k: rel_err(mg[k], mo[k]) for k in ("rho", "p")}
     errs["u"] = vel_err(mg, mo)
@@ -50,6 +50,15 @@ def _compare(case, fields, steps, tol=TOL64):
     for k, e in errs.items():
         assert e <= tol, (k, errs)
     return errs
+
+
+@pytest.mark.parametrize("tuning", [(1, 4), (1, 20), (1, 64), (2, 16)])
+@pytest.mark.parametrize("top", [O.TOP_FREESLIP, O.TOP_NOSLIP, O.TOP_PERIODIC])
+def test_fused_and_split_paths_fp64(tuning, top):
+    """The single-pass kernel (path 1) with several chunk heights (chunk seams
+    inside the droplet) and the two-kernel path (2) against the oracle."""
+    c = Case(70, 44, top=top, axis=0 if top == O.TOP_PERIODIC else 1)
+    _compare(c, _droplet_fields(c, 13, du=2e-3, seed=9), 80, tuning=tuning)
 
 
 def test_init_moments_roundtrip():
