@@ -139,11 +139,11 @@ int lbm_axi_time_kernels(lbm_axi* h, long long n, double* ms);
  *         collision in a single pass over the populations, 72 B per node in FP32);
  *         needs nr >= 16.  LBM_PATH_SPLIT -- kernel (a) (gather, rho, j, psi into
  *         field planes) then kernel (b) (forces + collision), 140 B per node.
- *   rows_per_cta: rows of each 64-wide z-strip one CTA of the fused kernel marches
- *         over (>= 4).
- * The default is FUSED when nr >= 16 with rows_per_cta chosen for about two
- * waves of CTAs.  The two paths agree to rounding.  Setting waits for the
- * handle's stream. */
+ *   rows_per_cta: 0 -- one wave of CTAs, each marching an equal share of the
+ *         (z-strip, row) space (default); > 0 -- fixed chunks of that many rows
+ *         of one z-strip per CTA.
+ * The default is FUSED (nr >= 16) with rows_per_cta = 0.  The paths agree to
+ * rounding.  Setting waits for the handle's stream. */
 enum { LBM_PATH_FUSED = 1, LBM_PATH_SPLIT = 2 };
 typedef struct {
     int path;

@@ -111,16 +111,6 @@ double stored_rho_ref(const lbm_axi* h) {
 
 int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
 
-// Default rows per CTA of the fused kernel: about two waves of four CTAs per SM.
-int default_rows_per_cta(int nz, int nr, int strip) {
-    const long long strips = (nz + strip - 1) / strip;
-    long long rows = (nr * strips + 1215) / 1216;
-    rows = (rows + 3) / 4 * 4;
-    if (rows < 16) rows = 16;
-    if (rows > 512) rows = 512;
-    return (int)rows;
-}
-
 // One step.  Fused path: kernel (b') reads f[cur] and writes f[cur^1].  Split
 // path: kernel (a) on the current populations, kernel (b) into the other buffer.
 cudaError_t enqueue_step(lbm_axi* h) {
@@ -334,8 +324,7 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     h->pf = make_params<float>(h);
     h->pdd = make_params<double>(h);
     h->path = nr >= lbm::kStepMinRows ? LBM_PATH_FUSED : LBM_PATH_SPLIT;
-    h->rows_per_cta = default_rows_per_cta(nz, nr, h->precision == 32 ? Ops<float>::step_strip()
-                                                                       : Ops<double>::step_strip());
+    h->rows_per_cta = 0;  // balanced single wave
     if (h->precision == 32) h->pdd = make_params_out(h);
     *h->herr = 0;
     cudaError_t err = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
@@ -561,7 +550,7 @@ int lbm_axi_set_tuning(lbm_axi* h, const lbm_axi_tuning* t) {
     if (!h || !t) return LBM_ERR_INVALID_ARG;
     if (t->path != LBM_PATH_FUSED && t->path != LBM_PATH_SPLIT) return LBM_ERR_INVALID_ARG;
     if (t->path == LBM_PATH_FUSED && h->nr < lbm::kStepMinRows) return LBM_ERR_INVALID_ARG;
-    if (t->rows_per_cta < 4 || t->rows_per_cta > (1 << 20)) return LBM_ERR_INVALID_ARG;
+    if (t->rows_per_cta < 0 || t->rows_per_cta > (1 << 20)) return LBM_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ERR_CUDA;
     if (h->graph) {

@@ -61,6 +61,24 @@ int Ops<R>::step_strip() {
     return StepTile<R>::TZ;
 }
 
+// The four compiled forms of the fused kernel (force on/off x axis terms on/off).
+template <typename R, bool MP, bool AX>
+static auto step_kernel() {
+    return k_step<R, StepTile<R>::TZ, StepTile<R>::RR, StepTile<R>::MINB, MP, AX>;
+}
+
+template <typename R>
+static cudaError_t set_step_attr(int smem) {
+    cudaError_t e = cudaFuncSetAttribute(step_kernel<R, true, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_kernel<R, true, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_kernel<R, false, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step_kernel<R, false, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
 template <typename R>
 cudaError_t Ops<R>::prepare() {
     using T = UpdateTile<R>;
@@ -70,18 +88,51 @@ cudaError_t Ops<R>::prepare() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_update<R, T::TZ, T::TR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_step<R, StepTile<R>::TZ, StepTile<R>::RR, StepTile<R>::MINB>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem());
+    if (e == cudaSuccess) e = set_step_attr<R>((int)step_smem());
     return e;
+}
+
+// CTAs of the fused kernel that fit on the device at once (one wave).
+template <typename R>
+static int step_resident_ctas() {
+    static int cached = 0;
+    if (cached > 0) return cached;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 152;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<R, true, true>(),
+                                                      StepShape<StepTile<R>::TZ, StepTile<R>::RR>::NT,
+                                                      Ops<R>::step_smem()) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    cached = sms * per_sm;
+    return cached;
 }
 
 template <typename R>
 cudaError_t Ops<R>::step(const Params<R>& p, const R* f, R* fout, int rows_per_cta, int* err, cudaStream_t s) {
-    if (rows_per_cta < 1) rows_per_cta = 1;
-    constexpr int TZ = StepTile<R>::TZ, RR = StepTile<R>::RR, MINB = StepTile<R>::MINB;
-    dim3 grid((p.nz + TZ - 1) / TZ, (p.nr + rows_per_cta - 1) / rows_per_cta);
-    k_step<R, TZ, RR, MINB><<<grid, StepShape<TZ, RR>::NT, step_smem(), s>>>(p, f, fout, rows_per_cta, err);
+    constexpr int TZ = StepTile<R>::TZ, RR = StepTile<R>::RR;
+    constexpr int NT = StepShape<TZ, RR>::NT;
+    dim3 grid;
+    if (rows_per_cta > 0) {
+        grid = dim3((p.nz + TZ - 1) / TZ, (p.nr + rows_per_cta - 1) / rows_per_cta);
+    } else {
+        // balanced single wave; no CTA gets less than 16 rows of work
+        const long long total = (long long)((p.nz + TZ - 1) / TZ) * p.nr;
+        long long n = step_resident_ctas<R>();
+        if (n > (total + 15) / 16) n = (total + 15) / 16;
+        grid = dim3((unsigned)(n > 0 ? n : 1));
+    }
+    const size_t smem = step_smem();
+    if (p.multiphase && p.axis)
+        k_step<R, TZ, RR, StepTile<R>::MINB, true, true><<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
+    else if (p.multiphase)
+        k_step<R, TZ, RR, StepTile<R>::MINB, true, false><<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
+    else if (p.axis)
+        k_step<R, TZ, RR, StepTile<R>::MINB, false, true><<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
+    else
+        k_step<R, TZ, RR, StepTile<R>::MINB, false, false><<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
     return cudaGetLastError();
 }
 

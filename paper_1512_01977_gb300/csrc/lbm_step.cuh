@@ -9,7 +9,7 @@
 //
 //   stage L  rows pb          pull 9 populations, rho, j, psi     width TZ+12
 //   stage D  rows pb - LAG    psi_z, psi_r                        width TZ+8
-//   stage U  rows pb - 2 LAG  F_K, psi_rr, psi_rz, F_axis, F, u    width TZ+4
+//   stage U  rows pb - 2 LAG  F_K, psi_rr, psi_rz, F_axis, F -> u  width TZ+4
 //   stage C  rows pb - 3 LAG  grad u, H, h_i, EDM + BGK, store     width TZ
 //
 // With that lag every stage reads only rows written in earlier iterations
@@ -112,7 +112,7 @@ struct StepShape {
     // one item per thread in every stage (the widest, stage L, sets the count)
     static constexpr int NT = (RR * WL + 31) / 32 * 32;
     static constexpr int DP = 16, DD = 16, DJ = 16, DU = 8;  // ring depths (rows)
-    static constexpr int elems = DP * WL + 2 * DD * WD + 3 * DJ * WU + 4 * DU * WU;
+    static constexpr int elems = DP * WL + 2 * DD * WD + 3 * DJ * WU + 2 * DU * WU;
     // schedule constraints (checked exhaustively on the CPU for RR = 2)
     static_assert(11 + 2 * RR <= DP && 7 + 2 * RR <= DD && 6 + 4 * RR <= DJ && 4 + 2 * RR <= DU, "ring depth");
 };
@@ -140,30 +140,27 @@ __device__ __forceinline__ void prefetch(const Params<R>& p, const R* __restrict
     if (valid) gather32(p, f, j, kc, fi);
 }
 
-template <typename R, int TZ, int RR, int MINB>
-__global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB) k_step(Params<R> p, const R* __restrict__ f, R* __restrict__ fout,
-                                                       int rows_per_cta, int* __restrict__ err) {
+// One CTA marches z-strip `strip` over rows [j0, jend).  MP / AX: pseudopotential
+// force and axisymmetric terms compiled in or out.
+template <typename R, int TZ, int RR, bool MP, bool AX>
+__device__ __forceinline__ void march(const Params<R>& p, const R* __restrict__ f, R* __restrict__ fout, int strip,
+                                      int j0, int jend, unsigned char* smem_raw, int& bad) {
     using S = StepShape<TZ, RR>;
-    constexpr int NT = S::NT, WL = S::WL, WD = S::WD, WU = S::WU, LAG = S::LAG;
+    constexpr int WL = S::WL, WD = S::WD, WU = S::WU, LAG = S::LAG;
     constexpr int DP = S::DP, DD = S::DD, DJ = S::DJ, DU = S::DU;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sPsi = reinterpret_cast<R*>(smem_raw);  // [DP][WL]
     R* sPz = sPsi + DP * WL;                   // [DD][WD]
     R* sPr = sPz + DD * WD;
     R* sRho = sPr + DD * WD;  // [DJ][WU]  rho - rho_ref
     R* sJz = sRho + DJ * WU;
     R* sJr = sJz + DJ * WU;
-    R* sUz = sJr + DJ * WU;  // [DU][WU]
+    R* sUz = sJr + DJ * WU;  // [DU][WU]  physical velocity
     R* sUr = sUz + DU * WU;
-    R* sFz = sUr + DU * WU;
-    R* sFr = sFz + DU * WU;
 
     const int tid = threadIdx.x;
-    const int k0 = blockIdx.x * TZ;
+    const int k0 = strip * TZ;
     const int kn = min(TZ, p.nz - k0);
-    const int j0 = blockIdx.y * rows_per_cta;
-    const int jend = min(j0 + rows_per_cta, p.nr);
-    const bool mp = p.multiphase != 0, ax = p.axis != 0;
+    constexpr bool mp = MP, ax = AX;
     const bool periodic = p.top == TOP_PERIODIC;
     const int plane = (int)p.plane;
 
@@ -194,7 +191,6 @@ __global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB) k_step(Params<R> 
     const R c9 = R(1) / R(9), c36 = R(1) / R(36);
     const R kA = p.A, kB = R(1) - R(2) * p.A;
     const int uz_top = p.top == TOP_NOSLIP ? -1 : 1;
-    int bad = 0;
 
     // Source row of a stage-L node (mirror or wrap for ghost rows).
     auto lsrc = [&](int row, int& sgn_r) {
@@ -314,8 +310,6 @@ __global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB) k_step(Params<R> 
                 const int ou = (row & (DU - 1)) * WU + c;
                 sUz[ou] = R(s_uz) * ((sJz[sj] + R(0.5) * fz) * irho);
                 sUr[ou] = R(s_ur) * ((sJr[sj] + R(0.5) * fr) * irho);
-                sFz[ou] = fz;
-                sFr[ou] = fr;
             }
         }
 
@@ -335,7 +329,8 @@ __global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB) k_step(Params<R> 
                 const R u0z = sJz[sj] * irho, u0r = sJr[sj] * irho;
                 const int ou = (row & (DU - 1)) * WU + c;
                 const R uz = sUz[ou], ur = sUr[ou];
-                const R duz = sFz[ou] * irho, dur = sFr[ou] * irho;
+                // EDM velocity shift F / rho from u = u0 + F / (2 rho)
+                const R duz = R(2) * (uz - u0z), dur = R(2) * (ur - u0r);
                 const R u1z = u0z + duz, u1r = u0r + dur;
                 R Hz = R(0), Hr = R(0), m0 = R(0);
                 if (ax) {
@@ -375,6 +370,34 @@ __global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB) k_step(Params<R> 
             }
         }
         __syncthreads();
+    }
+}
+
+// Grid: one CTA per resident slot.  The flattened strip-row space
+// (strip * nr + row) is cut into gridDim.x equal contiguous ranges; a CTA
+// marches each strip segment of its range (usually one or two).  rows_per_cta
+// > 0 instead gives fixed chunks: CTA (x, y) = strip x, rows [y R, y R + R).
+template <typename R, int TZ, int RR, int MINB, bool MP, bool AX>
+__global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB) k_step(Params<R> p, const R* __restrict__ f,
+                                                                      R* __restrict__ fout, int rows_per_cta,
+                                                                      int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int bad = 0;
+    if (rows_per_cta > 0) {
+        const int j0 = blockIdx.y * rows_per_cta;
+        march<R, TZ, RR, MP, AX>(p, f, fout, blockIdx.x, j0, min(j0 + rows_per_cta, p.nr), smem_raw, bad);
+    } else {
+        const int nstrips = (p.nz + TZ - 1) / TZ;
+        const long long total = (long long)nstrips * p.nr;
+        const long long per = (total + gridDim.x - 1) / gridDim.x;
+        long long a = (long long)blockIdx.x * per;
+        const long long b = min(a + per, total);
+        while (a < b) {
+            const int strip = (int)(a / p.nr), j0 = (int)(a - (long long)strip * p.nr);
+            const int jend = (int)min((long long)p.nr, j0 + (b - a));
+            march<R, TZ, RR, MP, AX>(p, f, fout, strip, j0, jend, smem_raw, bad);
+            a += jend - j0;
+        }
     }
     if (bad) atomicOr(err, bad);
 }

@@ -52,7 +52,7 @@ def _compare(case, fields, steps, tol=TOL64, tuning=None):
     return errs
 
 
-@pytest.mark.parametrize("tuning", [(1, 4), (1, 20), (1, 64), (2, 16)])
+@pytest.mark.parametrize("tuning", [(1, 0), (1, 4), (1, 20), (1, 64), (2, 16)])
 @pytest.mark.parametrize("top", [O.TOP_FREESLIP, O.TOP_NOSLIP, O.TOP_PERIODIC])
 def test_fused_and_split_paths_fp64(tuning, top):
     """The single-pass kernel (path 1) with several chunk heights (chunk seams
