@@ -171,6 +171,31 @@ int lbm_axi_mass(lbm_axi* h, double* mass_rweighted, double* mass_plain);
  * Returns LBM_ERR_INVALID_ARG if either region holds no node. */
 int lbm_axi_pressure_jump(lbm_axi* h, double z_c, double r_c, double r_in, double r_out, double* dp);
 
+/* Allocation-free mass reduction.  No counterpart in the paper: it serves
+ * callers that cannot let a library allocate device memory for them -- a
+ * serving loop running out of a fixed, pre-reserved arena, or a framework
+ * whose caching allocator must account for every device byte.  It computes
+ * d_out[0] = sum_{k,j} (j + 1/2) rho[j*nz + k] and d_out[1] = sum rho over a
+ * caller-owned device array of nz*nr doubles (e.g. the rho written by
+ * lbm_axi_moments_device), with the FP64 warp-shuffle reduction of
+ * lbm_axi_mass, and writes the two doubles to the caller-owned device buffer
+ * d_out.  The reduction's per-block partial sums live in a 64 KB static device
+ * array that every GPU loading the library holds until the process exits; the
+ * call allocates nothing.  Limits and behaviour:
+ *   - nz*nr must not exceed LBM_NOALLOC_MAX_NODES (8,388,608 = 4096 x 2048);
+ *     larger fields, NULL pointers or nz, nr < 1 return LBM_ERR_INVALID_ARG;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture on that device;
+ *   - work is enqueued on `stream` (a cudaStream_t, NULL = legacy default) and
+ *     the call returns without waiting; the result is in d_out once the
+ *     stream reaches it;
+ *   - every call shares the one array, so calls whose work overlaps on the
+ *     GPU (different streams, or threads without ordering) race and must be
+ *     serialised by the caller. */
+#define LBM_NOALLOC_MAX_NODES 8388608
+int lbm_axi_mass_field_noalloc(const double* d_rho, int nz, int nr, double* d_out, void* stream);
+
 /* Release the solve.  NULL is a no-op.  Waits for the handle's stream. */
 void lbm_axi_destroy(lbm_axi* h);
 

@@ -75,7 +75,10 @@ _SIGS = {
     "lbm_eos_pressure": (C.c_int, [C.POINTER(lbm_eos), C.c_double, _D, _D]),
     "lbm_axi_set_allocator": (C.c_int, [ALLOC_FN, RELEASE_FN, C.c_void_p]),
     "lbm_axi_strerror": (C.c_char_p, [C.c_int]),
+    "lbm_axi_mass_field_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
 }
+
+NOALLOC_MAX_NODES = 8388608
 
 
 def lib():
@@ -256,6 +259,20 @@ def lbm_eos_pressure(eos, rho):
     p, dp = C.c_double(), C.c_double()
     _check(lib().lbm_eos_pressure(C.byref(eos), float(rho), C.byref(p), C.byref(dp)), "lbm_eos_pressure")
     return p.value, dp.value
+
+
+def lbm_axi_mass_field_noalloc(d_rho, nz, nr, d_out, stream=None):
+    """Allocation-free FP64 mass reduction over a caller-owned device density
+    field (contiguous float64 CUDA tensor of nz*nr values) into a caller-owned
+    float64 CUDA tensor of 2 values: [sum (j+1/2) rho, sum rho].  Enqueued on
+    `stream` (a torch.cuda.Stream, a raw cudaStream_t or None); nothing is
+    allocated.  Fields larger than NOALLOC_MAX_NODES are rejected."""
+    if nz * nr > NOALLOC_MAX_NODES:
+        raise LbmError(ERR_INVALID_ARG, "lbm_axi_mass_field_noalloc: nz*nr = %d exceeds the maximum %d"
+                       % (nz * nr, NOALLOC_MAX_NODES))
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib().lbm_axi_mass_field_noalloc(_devptr(d_rho), int(nz), int(nr), _devptr(d_out), raw),
+           "lbm_axi_mass_field_noalloc")
 
 
 _alloc_keep = []
