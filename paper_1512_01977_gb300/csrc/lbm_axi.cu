@@ -36,38 +36,7 @@ int pitch_of(int nz) { return (nz + 31) / 32 * 32; }
 
 }  // namespace
 
-struct lbm_axi {
-    int nz, nr, pitch;
-    long long plane;
-    int precision;
-    double tau, A, T, Tc;
-    lbm_eos eos;
-    lbm_axi_opts opts;
-    int device;
-    void* f[2];
-    int cur;
-    void* aux;
-    double* mout;     // 4 planes of nz*nr doubles (moments / init staging)
-    double* partial;  // reduction partials
-    double* dred;     // reduction results (4 doubles)
-    int* derr;        // sticky device error word
-    int* herr;        // pinned copy
-    double* hred;     // pinned reduction results
-    cudaStream_t stream;
-    bool own_stream;
-    bool via_hook;
-    void* hook_ctx;
-    void (*hook_release)(void*, void*);
-    cudaGraphExec_t graph;
-    int graph_steps;
-    bool initialized;
-    int pending;  // error status carried to the next sync
-    size_t bytes;
-    int path;          // LBM_PATH_FUSED or LBM_PATH_SPLIT
-    int rows_per_cta;  // rows of a z-strip per CTA of the fused kernel
-    Params<float> pf;
-    Params<double> pdd;
-};
+#include "lbm_handle.h"
 
 namespace {
 
@@ -116,6 +85,19 @@ int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA
 cudaError_t enqueue_step(lbm_axi* h) {
     const int c = h->cur;
     cudaError_t e;
+    if (h->path == LBM_PATH_FUSED && h->rows_per_cta == 0) {
+        // balanced one-wave grid: the batched kernel with a batch of one, so a
+        // solve runs the same code alone as inside any batch
+        const bool mp = h->opts.multiphase != 0, ax = h->opts.axis_terms != 0;
+        if (h->precision == 32)
+            e = Ops<float>::step_batch(static_cast<const lbm::BatchSolve<float>*>(h->d_self), h->d_self_start, 1,
+                                       mp, ax, c, 128, 0, h->derr, h->stream);
+        else
+            e = Ops<double>::step_batch(static_cast<const lbm::BatchSolve<double>*>(h->d_self), h->d_self_start,
+                                        1, mp, ax, c, 128, 0, h->derr, h->stream);
+        h->cur = c ^ 1;
+        return e;
+    }
     if (h->path == LBM_PATH_FUSED) {
         if (h->precision == 32)
             e = Ops<float>::step(h->pf, (const float*)h->f[c], (float*)h->f[c ^ 1], h->rows_per_cta, h->derr,
@@ -213,6 +195,8 @@ void release_all(lbm_axi* h) {
     dev_free(h->partial, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->dred, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->derr, h->via_hook, h->hook_ctx, h->hook_release);
+    dev_free(h->d_self, h->via_hook, h->hook_ctx, h->hook_release);
+    dev_free(h->d_self_start, h->via_hook, h->hook_ctx, h->hook_release);
     if (h->herr) cudaFreeHost(h->herr);
     if (h->hred) cudaFreeHost(h->hred);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -300,8 +284,11 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     h->partial = (double*)dev_alloc(4 * lbm::kReduceBlocks * sizeof(double));
     h->dred = (double*)dev_alloc(4 * sizeof(double));
     h->derr = (int*)dev_alloc(sizeof(int));
+    h->d_self = dev_alloc(o.precision == 32 ? sizeof(lbm::BatchSolve<float>) : sizeof(lbm::BatchSolve<double>));
+    h->d_self_start = (long long*)dev_alloc(2 * sizeof(long long));
     h->bytes = lbm_axi_footprint(nz, nr, o.precision);
-    bool ok = h->f[0] && h->f[1] && h->aux && h->mout && h->partial && h->dred && h->derr;
+    bool ok = h->f[0] && h->f[1] && h->aux && h->mout && h->partial && h->dred && h->derr && h->d_self &&
+              h->d_self_start;
     ok = ok && cudaMallocHost(&h->herr, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost(&h->hred, 4 * sizeof(double)) == cudaSuccess;
     if (!ok) {
@@ -327,7 +314,20 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     h->rows_per_cta = 0;  // balanced single wave
     if (h->precision == 32) h->pdd = make_params_out(h);
     *h->herr = 0;
-    cudaError_t err = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
+    cudaError_t err = cudaSuccess;
+    {
+        // descriptor of this solve for the batched kernel (strip width 128)
+        const long long start[2] = {0, (long long)((nz + 127) / 128) * nr};
+        if (o.precision == 32) {
+            lbm::BatchSolve<float> d{h->pf, (const float*)h->f[0], (float*)h->f[1]};
+            err = cudaMemcpy(h->d_self, &d, sizeof(d), cudaMemcpyHostToDevice);
+        } else {
+            lbm::BatchSolve<double> d{h->pdd, (const double*)h->f[0], (double*)h->f[1]};
+            err = cudaMemcpy(h->d_self, &d, sizeof(d), cudaMemcpyHostToDevice);
+        }
+        if (err == cudaSuccess) err = cudaMemcpy(h->d_self_start, start, sizeof(start), cudaMemcpyHostToDevice);
+    }
+    if (err == cudaSuccess) err = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
     if (err == cudaSuccess) err = cudaMemsetAsync(h->aux, 0, 4 * plane_bytes, h->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
     if (err != cudaSuccess) {

@@ -56,6 +56,15 @@ struct Params {
     int top, axis, multiphase, kappa, hr_sign;
 };
 
+// One solve of a batched launch: its parameters and its two population buffers
+// (even batch steps read f_a and write f_b, odd steps the reverse).
+template <typename R>
+struct BatchSolve {
+    Params<R> p;
+    const R* f_a;
+    R* f_b;
+};
+
 // --------------------------------------------------------------------- EOS --
 // P_k(rho) of Eq. (kupershtokvdwpressure) or Carnahan-Starling.
 template <typename R>

@@ -1,0 +1,51 @@
+// Internal: the solve handle behind the opaque lbm_axi pointer (shared by the
+// single-solve API in lbm_axi.cu and the batch API in lbm_batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_axi.h"
+#include "lbm_device.cuh"
+
+using lbm::Params;
+
+struct lbm_axi {
+    int nz, nr, pitch;
+    long long plane;
+    int precision;
+    double tau, A, T, Tc;
+    lbm_eos eos;
+    lbm_axi_opts opts;
+    int device;
+    void* f[2];
+    int cur;
+    void* aux;
+    double* mout;     // 4 planes of nz*nr doubles (moments / init staging)
+    double* partial;  // reduction partials
+    double* dred;     // reduction results (4 doubles)
+    int* derr;        // sticky device error word
+    int* herr;        // pinned copy
+    double* hred;     // pinned reduction results
+    cudaStream_t stream;
+    bool own_stream;
+    bool via_hook;
+    void* hook_ctx;
+    void (*hook_release)(void*, void*);
+    cudaGraphExec_t graph;
+    int graph_steps;
+    bool initialized;
+    int pending;  // error status carried to the next sync
+    size_t bytes;
+    int path;          // LBM_PATH_FUSED or LBM_PATH_SPLIT
+    int rows_per_cta;  // fused path: 0 = balanced wave (the batched kernel, batch of one); > 0 = chunks
+    void* d_self;      // BatchSolve<R> of this solve (f_a = f[0], f_b = f[1]) for the batched kernel
+    long long* d_self_start;  // {0, strips * nr}
+    Params<float> pf;
+    Params<double> pdd;
+};
+
+// Step parity bookkeeping used by the batch API: after n steps run outside
+// the handle's own step loop, its current buffer flips when n is odd.
+inline void lbm_handle_advance(lbm_axi* h, long long n) {
+    if (n & 1) h->cur ^= 1;
+}

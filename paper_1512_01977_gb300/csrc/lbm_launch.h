@@ -38,6 +38,12 @@ struct Ops {
     static cudaError_t step(const Params<R>& p, const R* f, R* fout, int rows_per_cta, int* err, cudaStream_t s);
     static size_t step_smem();
     static int step_strip();  // z-columns per CTA of the single-pass kernel
+    // Batched fused step over nsolves solves (device arrays solves[n], start[n+1]).
+    // strip: 64 or 128 z-columns per CTA; grid: CTAs (0 = one resident wave).
+    static cudaError_t step_batch(const BatchSolve<R>* solves, const long long* start, int nsolves, bool mp,
+                                  bool ax, int parity, int strip, int grid, int* err, cudaStream_t s);
+    static int batch_resident_ctas(int strip);
+    static size_t batch_smem(int strip);
 };
 
 }  // namespace lbm

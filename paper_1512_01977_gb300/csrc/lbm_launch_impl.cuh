@@ -89,6 +89,10 @@ cudaError_t Ops<R>::prepare() {
         e = cudaFuncSetAttribute(k_update<R, T::TZ, T::TR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem);
     if (e == cudaSuccess) e = set_step_attr<R>((int)step_smem());
+    // the batched kernel (also the default single-solve step): attributes and
+    // occupancy are settled here, outside any stream capture
+    if (e == cudaSuccess && (batch_resident_ctas(64) <= 0 || batch_resident_ctas(128) <= 0))
+        e = cudaErrorInvalidConfiguration;
     return e;
 }
 
@@ -177,6 +181,93 @@ cudaError_t Ops<R>::pjump(const Params<R>& p, const Params<double>& pd, const R*
     k_pjump<R><<<kReduceBlocks, 256, 0, s>>>(p, pd, aux, zc, rc, rin, rout, partial);
     k_reduce_final<4><<<1, 32, 0, s>>>(partial, kReduceBlocks, out);
     return cudaGetLastError();
+}
+
+}  // namespace lbm
+
+namespace lbm {
+
+// Batched kernel forms: strip width 64 or 128 (the autotuner picks), force and
+// axis terms compiled in or out.
+template <typename R, int TZ>
+struct BatchTile {
+    static constexpr int RR = 2;
+    static constexpr int MINB = TZ == 128 ? 3 : 5;
+    static constexpr int NT = StepShape<TZ, RR>::NT;
+    static size_t smem() { return sizeof(R) * (size_t)StepShape<TZ, RR>::elems; }
+};
+
+template <typename R, int TZ, bool MP, bool AX>
+static auto batch_kernel() {
+    return k_step_batch<R, TZ, BatchTile<R, TZ>::RR, BatchTile<R, TZ>::MINB, MP, AX>;
+}
+
+template <typename R, int TZ>
+static cudaError_t batch_prepare() {
+    const int smem = (int)BatchTile<R, TZ>::smem();
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel<R, TZ, true, true>(),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_kernel<R, TZ, true, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_kernel<R, TZ, false, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batch_kernel<R, TZ, false, false>(),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
+template <typename R>
+size_t Ops<R>::batch_smem(int strip) {
+    return strip == 64 ? BatchTile<R, 64>::smem() : BatchTile<R, 128>::smem();
+}
+
+template <typename R>
+int Ops<R>::batch_resident_ctas(int strip) {
+    static int cached[2] = {0, 0};
+    const int slot = strip == 64 ? 0 : 1;
+    if (cached[slot] > 0) return cached[slot];
+    if ((strip == 64 ? batch_prepare<R, 64>() : batch_prepare<R, 128>()) != cudaSuccess) return 0;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    cudaError_t e = strip == 64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                      &per_sm, batch_kernel<R, 64, true, true>(), BatchTile<R, 64>::NT,
+                                      BatchTile<R, 64>::smem())
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                      &per_sm, batch_kernel<R, 128, true, true>(), BatchTile<R, 128>::NT,
+                                      BatchTile<R, 128>::smem());
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    cached[slot] = sms * per_sm;
+    return cached[slot];
+}
+
+template <typename R, int TZ>
+static cudaError_t launch_batch(const BatchSolve<R>* solves, const long long* start, int n, bool mp, bool ax,
+                                int parity, int grid, int* err, cudaStream_t s) {
+    using T = BatchTile<R, TZ>;
+    const size_t smem = T::smem();
+    if (mp && ax)
+        batch_kernel<R, TZ, true, true>()<<<grid, T::NT, smem, s>>>(solves, start, n, parity, err);
+    else if (mp)
+        batch_kernel<R, TZ, true, false>()<<<grid, T::NT, smem, s>>>(solves, start, n, parity, err);
+    else if (ax)
+        batch_kernel<R, TZ, false, true>()<<<grid, T::NT, smem, s>>>(solves, start, n, parity, err);
+    else
+        batch_kernel<R, TZ, false, false>()<<<grid, T::NT, smem, s>>>(solves, start, n, parity, err);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Ops<R>::step_batch(const BatchSolve<R>* solves, const long long* start, int n, bool mp, bool ax,
+                               int parity, int strip, int grid, int* err, cudaStream_t s) {
+    if (grid <= 0) grid = batch_resident_ctas(strip);
+    if (grid <= 0) return cudaErrorInvalidConfiguration;
+    return strip == 64 ? launch_batch<R, 64>(solves, start, n, mp, ax, parity, grid, err, s)
+                       : launch_batch<R, 128>(solves, start, n, mp, ax, parity, grid, err, s);
 }
 
 }  // namespace lbm

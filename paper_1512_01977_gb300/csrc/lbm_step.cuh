@@ -402,4 +402,43 @@ __global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB) k_step(Params<R> 
     if (bad) atomicOr(err, bad);
 }
 
+// ------------------------------------------------------------ batched step --
+// Many independent solves advanced by one launch.  The strip-row spaces of the
+// solves are concatenated (solve s occupies [start[s], start[s+1])); a
+// one-wave grid cuts the concatenation into equal contiguous shares, and each
+// CTA marches the (solve, strip, rows) segments of its share.  Even batch
+// steps read f_a and write f_b, odd steps the reverse.
+template <typename R, int TZ, int RR, int MINB, bool MP, bool AX>
+__global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB)
+    k_step_batch(const BatchSolve<R>* __restrict__ solves, const long long* __restrict__ start, int nsolves,
+                 int parity, int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ Params<R> sp;
+    const long long total = start[nsolves];
+    const long long per = (total + gridDim.x - 1) / gridDim.x;
+    long long a = (long long)blockIdx.x * per;
+    const long long b = min(a + per, total);
+    while (a < b) {
+        int lo = 0, hi = nsolves - 1;  // last solve with start <= a
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (start[mid] <= a) lo = mid;
+            else hi = mid - 1;
+        }
+        const int s = lo;
+        __syncthreads();  // everyone is done with the previous segment's parameters
+        if (threadIdx.x == 0) sp = solves[s].p;
+        __syncthreads();
+        const long long off = a - start[s];
+        const int strip = (int)(off / sp.nr), j0 = (int)(off - (long long)strip * sp.nr);
+        const int jend = (int)min((long long)sp.nr, j0 + (b - a));
+        const R* fin = parity ? solves[s].f_b : solves[s].f_a;
+        R* fo = parity ? const_cast<R*>(solves[s].f_a) : solves[s].f_b;
+        int bad = 0;
+        march<R, TZ, RR, MP, AX>(sp, fin, fo, strip, j0, jend, smem_raw, bad);
+        if (bad) atomicOr(&err[s], bad);
+        a += jend - j0;
+    }
+}
+
 }  // namespace lbm

@@ -37,6 +37,10 @@ class lbm_axi_tuning(C.Structure):
     _fields_ = [("path", C.c_int), ("rows_per_cta", C.c_int)]
 
 
+class lbm_axi_batch_tuning(C.Structure):
+    _fields_ = [("strip", C.c_int), ("grid", C.c_int)]
+
+
 class LbmError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -76,6 +80,18 @@ _SIGS = {
     "lbm_axi_set_allocator": (C.c_int, [ALLOC_FN, RELEASE_FN, C.c_void_p]),
     "lbm_axi_strerror": (C.c_char_p, [C.c_int]),
     "lbm_axi_mass_field_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
+    # include/lbm_axi_batch.h
+    "lbm_axi_batch_create": (C.c_int, [C.POINTER(_H), C.c_int, C.c_void_p, C.POINTER(_H)]),
+    "lbm_axi_batch_step": (C.c_int, [_H, C.c_longlong]),
+    "lbm_axi_batch_step_async": (C.c_int, [_H, C.c_longlong]),
+    "lbm_axi_batch_sync": (C.c_int, [_H]),
+    "lbm_axi_batch_status": (C.c_int, [_H, C.POINTER(C.c_int)]),
+    "lbm_axi_batch_steps": (C.c_int, [_H, C.POINTER(C.c_longlong)]),
+    "lbm_axi_batch_get_tuning": (C.c_int, [_H, C.POINTER(lbm_axi_batch_tuning)]),
+    "lbm_axi_batch_set_tuning": (C.c_int, [_H, C.POINTER(lbm_axi_batch_tuning)]),
+    "lbm_axi_batch_autotune": (C.c_int, [_H, C.c_int, C.POINTER(lbm_axi_batch_tuning)]),
+    "lbm_axi_autotune": (C.c_int, [_H, C.c_int, C.POINTER(lbm_axi_tuning)]),
+    "lbm_axi_batch_destroy": (None, [_H]),
 }
 
 NOALLOC_MAX_NODES = 8388608
@@ -273,6 +289,101 @@ def lbm_axi_mass_field_noalloc(d_rho, nz, nr, d_out, stream=None):
     raw = getattr(stream, "cuda_stream", stream)
     _check(lib().lbm_axi_mass_field_noalloc(_devptr(d_rho), int(nz), int(nr), _devptr(d_out), raw),
            "lbm_axi_mass_field_noalloc")
+
+
+# ------------------------------------------------------------ batched API --
+
+def lbm_axi_batch_create(handles, stream=None):
+    arr = (_H * len(handles))(*[h.value if isinstance(h, _H) else h for h in handles])
+    b = _H()
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(lib().lbm_axi_batch_create(arr, len(handles), raw, C.byref(b)), "lbm_axi_batch_create")
+    return b
+
+
+def lbm_axi_batch_step(b, n):
+    _check(lib().lbm_axi_batch_step(b, int(n)), "lbm_axi_batch_step")
+
+
+def lbm_axi_batch_step_async(b, n):
+    _check(lib().lbm_axi_batch_step_async(b, int(n)), "lbm_axi_batch_step_async")
+
+
+def lbm_axi_batch_sync(b):
+    """Wait; returns LBM_OK or the first error code (per-solve detail: lbm_axi_batch_status)."""
+    return lib().lbm_axi_batch_sync(b)
+
+
+def lbm_axi_batch_status(b, n):
+    st = (C.c_int * n)()
+    rc = lib().lbm_axi_batch_status(b, st)
+    if rc not in (OK, ERR_UNPHYSICAL):
+        raise LbmError(rc, "lbm_axi_batch_status")
+    return list(st)
+
+
+def lbm_axi_batch_get_tuning(b):
+    t = lbm_axi_batch_tuning()
+    _check(lib().lbm_axi_batch_get_tuning(b, C.byref(t)), "lbm_axi_batch_get_tuning")
+    return t.strip, t.grid
+
+
+def lbm_axi_batch_set_tuning(b, strip, grid):
+    t = lbm_axi_batch_tuning(strip, grid)
+    _check(lib().lbm_axi_batch_set_tuning(b, C.byref(t)), "lbm_axi_batch_set_tuning")
+
+
+def lbm_axi_batch_autotune(b, trials=5):
+    t = lbm_axi_batch_tuning()
+    _check(lib().lbm_axi_batch_autotune(b, int(trials), C.byref(t)), "lbm_axi_batch_autotune")
+    return t.strip, t.grid
+
+
+def lbm_axi_autotune(h, trials=5):
+    t = lbm_axi_tuning()
+    _check(lib().lbm_axi_autotune(h, int(trials), C.byref(t)), "lbm_axi_autotune")
+    return t.path, t.rows_per_cta
+
+
+def lbm_axi_batch_destroy(b):
+    lib().lbm_axi_batch_destroy(b)
+
+
+class Batch:
+    """Solves advanced together (one launch per step).  Borrows the Solver objects."""
+
+    def __init__(self, solvers, stream=None):
+        self.solvers = list(solvers)
+        self.b = lbm_axi_batch_create([s.h for s in self.solvers], stream)
+
+    def step(self, n):
+        rc = lib().lbm_axi_batch_step(self.b, int(n))
+        if rc not in (OK, ERR_UNPHYSICAL):
+            raise LbmError(rc, "lbm_axi_batch_step")
+        return rc
+
+    def step_async(self, n):
+        lbm_axi_batch_step_async(self.b, n)
+
+    def sync(self):
+        return lbm_axi_batch_sync(self.b)
+
+    def status(self):
+        return lbm_axi_batch_status(self.b, len(self.solvers))
+
+    def autotune(self, trials=5):
+        return lbm_axi_batch_autotune(self.b, trials)
+
+    def close(self):
+        if self.b:
+            lbm_axi_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _alloc_keep = []
