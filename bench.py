@@ -48,6 +48,12 @@ def _args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="wave", choices=["wave", "batched", "served"],
+                    help="wave: the 4096x2048 density wave (headline); batched: 256 uneven droplets in one "
+                         "launch per step vs one solve at a time; served: Poisson request stream with "
+                         "continuous batching vs a one-at-a-time server")
+    ap.add_argument("--requests", type=int, default=48, help="served: requests per arrival rate")
+    ap.add_argument("--budget-mb", type=int, default=4096, help="served: HBM admission budget")
     return ap.parse_args()
 
 
@@ -95,7 +101,7 @@ def _source_hash():
 def _ncu_traffic():
     """Per-launch DRAM bytes of the fused step kernel on this workload from the
     committed ncu summary, or None when the kernel sources changed since."""
-    path = os.path.join(ROOT, "profiles", "k_step_fp32_wave4096x2048.md")
+    path = os.path.join(ROOT, "profiles", "k_step_batch_fp32_wave4096x2048.md")
     try:
         vals = {}
         with open(path) as fh:
@@ -306,8 +312,8 @@ def run_ours(args):
                        "parallelism": "replicas only (independent solves per GPU)",
                        "device": props.name},
             "roofline": {"bound": "hbm",
-                         "kernel": "k_step (one-pass gather+psi+forces+EDM+source+collide)" if path == lbm.PATH_FUSED
-                         else "k_update (forces+EDM+source+collide)",
+                         "kernel": "k_step_batch (one-pass gather+psi+forces+EDM+source+collide; a batch of one)"
+                         if path == lbm.PATH_FUSED else "k_update (forces+EDM+source+collide)",
                          "achieved": ach_b, "peak": peak, "unit": "GB/s", "frac": ach_b / peak,
                          "peak_source": peak_kind, "traffic": traffic,
                          "algorithmic_bytes_per_node": bytes_main, "avg_launch_us": t_b * 1e6,
@@ -330,10 +336,115 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batched(args):
+    """256 independent droplets (sizes log-uniform 64x32 .. 512x256, R = 0.25 of
+    the shorter side, T/Tc ~ U[0.5, 0.85], tau ~ U[0.6, 1.0], CS, FP32 with
+    deviations about rho_v), `--steps` steps each: one batched launch per step
+    (autotuned) against the same solves stepped one at a time."""
+    import torch
+
+    import __graft_entry__
+    from paper_1512_01977_gb300 import inputs as I
+    from paper_1512_01977_gb300 import lbm
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    specs = I.batch_droplets(n=256, seed=4)
+    steps = args.steps
+
+    def make():
+        out = []
+        for sp in specs:
+            eos = lbm.make_eos(lbm.EOS_CS, sp["T_over_Tc"])
+            rv, rl = lbm.lbm_eos_coexistence(eos)
+            s = lbm.Solver(sp["nz"], sp["nr"], sp["tau"], eos=eos, A=A, precision=32, rho_ref=rv)
+            s.init(*I.droplet(sp["nz"], sp["nr"], sp["R"], rl, rv))
+            out.append(s)
+        return out
+
+    nodes = sum(sp["nz"] * sp["nr"] for sp in specs)
+    # one at a time: each solve's own CUDA-graph step loop
+    solvers = make()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    failed_seq = 0
+    for s in solvers:
+        try:
+            s.step(steps)
+        except lbm.LbmError:
+            failed_seq += 1
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    for s in solvers:
+        s.close()
+    # batched
+    solvers = make()
+    b = lbm.Batch(solvers)
+    tuning = b.autotune(trials=3)
+    b.step(args.warmup)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    b.step_async(steps)
+    b.sync()
+    t_batch = time.perf_counter() - w0
+    status = b.status()
+    b.close()
+    for s in solvers:
+        s.close()
+    value = nodes * steps / t_batch / 1e6
+    print(json.dumps({
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": t_batch * 1e3 / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "256 droplets, log-uniform 64x32..512x256, one launch per step", "solves": 256,
+                   "nodes": nodes, "tuning_strip_grid": list(tuning)},
+        "one_at_a_time": {"value": nodes * steps / t_seq / 1e6, "unit": "MLUPS", "wall_s": t_seq,
+                          "failed": failed_seq},
+        "speedup_vs_one_at_a_time": t_seq / t_batch,
+        "failed": sum(1 for x in status if x != lbm.OK),
+        "gpu_launches": steps,
+    }))
+
+
+def run_served(args):
+    """Poisson request streams (rates 10..1000/s): continuous batching vs one
+    request at a time; p50 / p99 latency and MLUPS per rate."""
+    import torch
+
+    import __graft_entry__
+    from paper_1512_01977_gb300 import inputs as I
+    from paper_1512_01977_gb300 import serve
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    rows = []
+    for rate in (10, 30, 100, 300, 1000):
+        reqs = I.request_stream(rate, args.requests, seed=5)
+        _, st = serve.serve(reqs, budget_bytes=args.budget_mb << 20)
+        _, sq = serve.serve_sequential(reqs)
+        rows.append({"rate_per_s": rate, "batched": st, "one_at_a_time": sq})
+    best = max(r["batched"]["mlups"] for r in rows)
+    print(json.dumps({
+        "metric": "MLUPS", "value": best, "unit": "MLUPS", "n_gpus": 1, "steps": None, "warmup": 0,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "served Poisson stream, droplets + waves, CS/vdW, T/Tc 0.5..0.9, "
+                               "grids 32x32..1024x512, 1k..20k steps", "requests_per_rate": args.requests,
+                   "budget_mb": args.budget_mb},
+        "rates": rows,
+    }))
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_ours(args)
 

@@ -206,7 +206,8 @@ __device__ __forceinline__ void march(const Params<R>& p, const R* __restrict__ 
     {
         int sg;
         const int row = j0 - 6 + l_rr;
-        prefetch(p, f, l_valid(row), lsrc(row, sg), lkc, lpf);
+        const bool v = l_valid(row);
+        prefetch(p, f, v, v ? lsrc(row, sg) : 0, lkc, lpf);
         const int crw = j0 - 6 - 3 * LAG + c_rr;
         prefetch(p, f, c_valid(crw), crw, ckc, cpf);
     }
@@ -240,7 +241,8 @@ __device__ __forceinline__ void march(const Params<R>& p, const R* __restrict__ 
             // issue the next iteration's gather now; it lands behind this iteration's arithmetic
             int sg;
             const int nrow = row + RR;
-            prefetch(p, f, l_valid(nrow), lsrc(nrow, sg), lkc, lpf);
+            const bool nv = l_valid(nrow);  // (inactive items sit far out of range: no map_row for them)
+            prefetch(p, f, nv, nv ? lsrc(nrow, sg) : 0, lkc, lpf);
         }
 
         // ---- stage D: rows pb-LAG ..: psi_z, psi_r (only with F_axis).
