@@ -219,15 +219,15 @@ def run_ours(args):
 
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     import __graft_entry__
     from paper_1512_01977_gb300 import lbm
 
+    from paper_1512_01977_gb300 import replicas
+
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
-    if ws > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    rep = replicas.Replicas(device=torch.device("cuda", local))
     __graft_entry__.build()
 
     eos = lbm.make_eos(lbm.EOS_CS, T_OVER_TC)
@@ -247,9 +247,7 @@ def run_ours(args):
     lbm.lbm_axi_step(s.h, args.warmup)
 
     def barrier():
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
+        rep.barrier()
 
     # ---- device-timed throughput: K steps, inputs resident in HBM
     props = torch.cuda.get_device_properties(local)
@@ -264,11 +262,8 @@ def run_ours(args):
     lbm.lbm_axi_sync(s.h)
     barrier()
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ws * n * args.steps / (ms_max * 1e3)  # MLUPS
+    ms_max = rep.max(ms)
+    value = replicas.aggregate_rate(n * args.steps, ws, ms_max * 1e-3) / 1e6  # MLUPS
 
     # ---- per-kernel device time (CUDA events around each launch, same stream)
     path, rows_per_cta = lbm.lbm_axi_get_tuning(s.h)
@@ -292,10 +287,7 @@ def run_ours(args):
         raise lbm.LbmError(rc, "lbm_axi_moments")
     barrier()
     wall = time.perf_counter() - w0
-    tw = torch.tensor([wall], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(tw, op=dist.ReduceOp.MAX)
-    e2e = ws * n * args.steps / (float(tw.item()) * 1e6)
+    e2e = replicas.aggregate_rate(n * args.steps, ws, rep.max(wall)) / 1e6
     mass_rw, _ = s.mass()
     s.close()
 
@@ -332,8 +324,7 @@ def run_ours(args):
         if cpu is not None:
             out["cpu_baseline"] = cpu
         print(json.dumps(out))
-    if ws > 1:
-        dist.destroy_process_group()
+    rep.close()
 
 
 def run_batched(args):
