@@ -44,30 +44,36 @@ def plane_poiseuille(g, R, nu, r):
     return g * (R**2 - np.asarray(r) ** 2) / (2.0 * nu)
 
 
-def fit_damped_cosine(t, y):
-    """Least-squares fit y = a + b exp(-c t) cos(w t + d); returns (w, c)."""
+def fit_damped_cosine(t, y, w_guess=None):
+    """Least-squares fit y = a + b exp(-c t) cos(w t + d) + e t; returns (w, c).
+
+    Starts from a scan of frequencies (around w_guess when given, else around
+    the zero-crossing estimate) and phases and keeps the best fit; the linear
+    term absorbs a slow drift of the mean (e.g. a droplet still relaxing)."""
     from scipy import optimize
 
     t = np.asarray(t, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     yc = y - y.mean()
-    # initial frequency from zero crossings
-    s = np.sign(yc)
-    idx = np.nonzero(s[1:] * s[:-1] < 0)[0]
-    if len(idx) >= 2:
-        w0 = np.pi / np.mean(np.diff(t[idx]))
-    else:
-        w0 = 2 * np.pi / (t[-1] - t[0])
+    if w_guess is None:
+        s = np.sign(yc)
+        idx = np.nonzero(s[1:] * s[:-1] < 0)[0]
+        w_guess = np.pi / np.mean(np.diff(t[idx])) if len(idx) >= 2 else 2 * np.pi / (t[-1] - t[0])
     a0, b0 = y.mean(), (y.max() - y.min()) / 2
+    span = t[-1] - t[0]
 
     def model(p, tt):
-        a, b, c, w, d = p
-        return a + b * np.exp(-c * tt) * np.cos(w * tt + d)
+        a, b, c, w, d, e = p
+        return a + b * np.exp(-np.clip(c * (tt - t[0]), -50, 50)) * np.cos(w * tt + d) + e * (tt - t[0])
 
     best = None
-    for d0 in np.linspace(0, 2 * np.pi, 8, endpoint=False):
-        res = optimize.least_squares(lambda p: model(p, t) - y, [a0, b0, 0.0, w0, d0])
-        if best is None or res.cost < best.cost:
-            best = res
-    a, b, c, w, d = best.x
+    for wf in (0.5, 0.7, 0.85, 1.0, 1.2, 1.5, 2.0):
+        for d0 in np.linspace(0, 2 * np.pi, 6, endpoint=False):
+            try:
+                res = optimize.least_squares(lambda p: model(p, t) - y, [a0, b0, 1.0 / span, w_guess * wf, d0, 0.0])
+            except ValueError:
+                continue
+            if best is None or res.cost < best.cost:
+                best = res
+    a, b, c, w, d, e = best.x
     return abs(w), c

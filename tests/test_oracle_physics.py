@@ -288,3 +288,16 @@ def test_table1_axis_matches_2d_with_ck_substitution():
     o2.step(4000)
     R2, dp2 = _laplace(o2.moments(), rv, rl, R0, False, 2 * R0, 2 * R0)
     assert dp * R == pytest.approx(dp2 * R2, rel=0.032)
+
+
+def test_damped_cosine_fit_recovers_frequency_over_a_drift():
+    """The oscillation-period fit: a known damped cosine on a linearly
+    drifting mean, sampled over about one period, gives back its frequency
+    and decay rate (the zero-crossing start alone locks onto the drift)."""
+    t = np.arange(0, 12000, 100.0)
+    w, c = 8.4e-4, 4.0e-4
+    y = 120 + 7 * np.exp(-c * t) * np.cos(w * t + 0.3) - 2e-4 * t
+    wf, cf = O.analytic.fit_damped_cosine(t, y, w_guess=1.1 * w)
+    assert wf == pytest.approx(w, rel=1e-6) and cf == pytest.approx(c, rel=1e-5)
+    wf, _ = O.analytic.fit_damped_cosine(t, y + 1e-3 * np.sin(0.37 * t))
+    assert wf == pytest.approx(w, rel=1e-3)
