@@ -80,6 +80,7 @@ def lib():
             "orc_stream": (None, [P, _D, _D]),
             "orc_run": (C.c_int, [P, _D, C.c_long]),
             "orc_init": (None, [P, _D, _D, _D, _D]),
+            "orc_init_physical": (C.c_int, [P, _D, _D, _D, _D]),
             "orc_moments": (C.c_int, [P, _D] + [_D] * 8),
             "orc_collide_only": (C.c_int, [P, _D, _D]),
             "orc_mass_rweighted": (C.c_double, [P, _D]),
@@ -203,12 +204,19 @@ class Oracle:
         self.params = params
         self.f = np.zeros((Q, params.nr, params.nz))
 
-    def init(self, rho, uz=None, ur=None):
+    def init(self, rho, uz=None, ur=None, physical=False):
+        """f = f^eq(rho, u).  physical=False: u is the bare velocity u0;
+        physical=True: u is the fluid velocity u0 + F/(2 rho) (at rest for u = 0)."""
         p = self.params
         rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(p.nr, p.nz)
         uz = np.zeros_like(rho) if uz is None else np.ascontiguousarray(uz, dtype=np.float64).reshape(rho.shape)
         ur = np.zeros_like(rho) if ur is None else np.ascontiguousarray(ur, dtype=np.float64).reshape(rho.shape)
-        lib().orc_init(C.byref(p.c()), _ptr(rho), _ptr(uz), _ptr(ur), _ptr(self.f))
+        if physical:
+            rc = lib().orc_init_physical(C.byref(p.c()), _ptr(rho), _ptr(uz), _ptr(ur), _ptr(self.f))
+            if rc != 0:
+                raise OracleError("oracle init failed with code %d" % rc)
+        else:
+            lib().orc_init(C.byref(p.c()), _ptr(rho), _ptr(uz), _ptr(ur), _ptr(self.f))
         return self
 
     def step(self, n=1):

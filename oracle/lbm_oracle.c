@@ -465,6 +465,35 @@ void orc_init(const orc_params* P, const double* rho, const double* uz, const do
     }
 }
 
+/* Start with the given u as the PHYSICAL velocity (a fluid at rest when u = 0).
+ * Sec. II.A defines the fluid velocity as u = u0 + F/(2 rho), u0 = sum_i c_i f_i / rho;
+ * Sec. III starts its droplets from the equilibrium densities with the fluid at
+ * rest.  So f = f^eq(rho, u - F/(2 rho)), with F = F_K + F_axis + rho g the force
+ * of the density field itself (first evaluated on f^eq(rho, u), whose density is
+ * rho up to rounding).  Returns ORC_ERR_UNPHYSICAL like a step. */
+int orc_init_physical(const orc_params* P, const double* rho, const double* uz, const double* ur, double* f) {
+    orc_init(P, rho, uz, ur, f);
+    orc_work w;
+    if (orc_work_alloc(P, &w)) {
+        orc_work_free(&w);
+        return -2;
+    }
+    int rc = orc_fields(P, f, &w);
+    if (rc == ORC_OK) {
+        long n = (long)P->nz * P->nr;
+        for (int j = 0; j < P->nr; j++) {
+            for (int k = 0; k < P->nz; k++) {
+                long c = (long)j * P->nz + k, e = orc_ext(P, k, j);
+                double feq[ORC_Q];
+                orc_feq(rho[c], uz[c] - w.Fz[e] / (2.0 * w.rho[e]), ur[c] - w.Fr[e] / (2.0 * w.rho[e]), feq);
+                for (int i = 0; i < ORC_Q; i++) f[i * n + c] = feq[i];
+            }
+        }
+    }
+    orc_work_free(&w);
+    return rc;
+}
+
 /* Macroscopic output of the current state: rho, physical u = u0 + F/(2 rho),
  * P_k(rho) (or rho/3 for a single-phase run).  Optional diagnostics (may be
  * NULL): the total force and H fields of the step that would follow. */

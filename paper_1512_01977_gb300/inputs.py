@@ -45,6 +45,18 @@ def droplet(nz, nr, R, rho_l, rho_v, width=2.0, zc=None, eps=0.0):
     return rho, np.zeros_like(rho), np.zeros_like(rho)
 
 
+def ellipsoid(nz, nr, Ra, Rz, rho_l, rho_v, width=2.0, zc=None):
+    """Axisymmetric ellipsoidal drop (r/Ra)^2 + ((z - zc)/Rz)^2 = 1 on the
+    axis (semi-axes Ra radially, Rz along z), with the tanh profile applied
+    to the scaled distance sqrt(...) times the equal-volume radius."""
+    Z, Rr = grid(nz, nr)
+    zc = nz / 2.0 if zc is None else zc
+    Rm = (Ra * Ra * Rz) ** (1.0 / 3.0)
+    s = np.sqrt((Rr / Ra) ** 2 + ((Z - zc) / Rz) ** 2)
+    rho = tanh_profile(s * Rm, Rm, rho_l, rho_v, width)
+    return rho, np.zeros_like(rho), np.zeros_like(rho)
+
+
 def droplet_2d(nz, nr, R, rho_l, rho_v, width=2.0):
     """Planar (2D) droplet centred in a fully periodic nz x nr box."""
     Z, Rr = grid(nz, nr)

@@ -301,3 +301,48 @@ def test_damped_cosine_fit_recovers_frequency_over_a_drift():
     assert wf == pytest.approx(w, rel=1e-6) and cf == pytest.approx(c, rel=1e-5)
     wf, _ = O.analytic.fit_damped_cosine(t, y + 1e-3 * np.sin(0.37 * t))
     assert wf == pytest.approx(w, rel=1e-3)
+
+
+def test_init_physical_is_plain_init_for_uniform_density():
+    """A uniform density exerts no force (every stencil sum of a constant psi
+    cancels), so starting with a physical velocity is starting with that bare
+    velocity -- up to the rounding of rho = sum_i f_i^eq(rho, u), which leaves
+    psi constant only to an ulp."""
+    nz, nr = 24, 12
+    p = O.make_params(nz, nr, 0.8, O.EOS_VDW, 0.8)
+    rho = np.full((nr, nz), 1.3)
+    _, uz, ur = I.random_state(nz, nr, 1.0, 0.0, 0.03, 5)
+    a = O.Oracle(p).init(rho, uz, ur)
+    b = O.Oracle(p).init(rho, uz, ur, physical=True)
+    np.testing.assert_allclose(b.f, a.f, rtol=1e-14, atol=0)
+
+
+def test_init_physical_starts_a_droplet_at_rest():
+    """With physical=True and u = 0 the fluid velocity u0 + F/(2 rho) of the
+    first state vanishes (Sec. II.A), while the bare start leaves F/(2 rho),
+    of order 1e-2 in the interface."""
+    nz, nr = 64, 32
+    p = O.make_params(nz, nr, 0.7, O.EOS_VDW, 0.8, A=0.0)
+    rv, rl = O.eos.maxwell_densities(p)
+    rho, _, _ = I.droplet(nz, nr, 12, rl, rv)
+    m = O.Oracle(p).init(rho, physical=True).moments()
+    assert np.abs(m["uz"]).max() < 1e-14 and np.abs(m["ur"]).max() < 1e-14
+    mb = O.Oracle(p).init(rho).moments()
+    assert np.hypot(mb["uz"], mb["ur"]).max() > 1e-3
+
+
+def test_oscillation_settings_run_from_rest():
+    """The oscillating-droplet settings of Sec. III (vdW, T = 0.8 T_c, A = 0,
+    tau = 0.7, density ratio about 10): started at rest the droplet relaxes
+    with spurious currents below 1e-2; started from the bare velocity, the
+    force F/(2 rho) of the sharp initial interface feeds the mass source
+    -rho u_r / r and the run goes unphysical within a few hundred steps."""
+    nz, nr = 160, 80
+    p = O.make_params(nz, nr, 0.7, O.EOS_VDW, 0.8, A=0.0)
+    rv, rl = O.eos.maxwell_densities(p)
+    rho, _, _ = I.droplet(nz, nr, 32, rl, rv)
+    o = O.Oracle(p).init(rho, physical=True).step(600)
+    m = o.moments()
+    assert np.hypot(m["uz"], m["ur"]).max() < 1e-2
+    with pytest.raises(O.OracleError):
+        O.Oracle(p).init(rho).step(600)
