@@ -112,6 +112,23 @@ int lbm_axi_init(lbm_axi* h, const double* rho, const double* u_z, const double*
 /* Same as lbm_axi_init with device arrays (nz*nr doubles, [j*nz + k]). */
 int lbm_axi_init_device(lbm_axi* h, const double* d_rho, const double* d_u_z, const double* d_u_r);
 
+/* Set the populations so that the given u is the PHYSICAL (fluid) velocity
+ * u = u0 + F/(2 rho) of Sec. II.A, where u0 = sum_i c_i f_i / rho is the bare
+ * velocity and F = F_K + F_axis (+ rho g_z) the force of the density field
+ * itself: f_i = f_i^eq(rho, u - F/(2 rho)).  With u = 0 the fluid starts at
+ * rest, the start of the droplet tests of Sec. III (equilibrium densities, no
+ * flow); lbm_axi_init instead leaves a spurious F/(2 rho) in every interface
+ * at t = 0.  F is evaluated on f^eq(rho, u) (density rho up to rounding).
+ * rho is required; u_z and u_r may be NULL (zero).  Host arrays, nz*nr
+ * doubles; a temporary device copy is made.  Synchronous.  Returns
+ * LBM_ERR_UNPHYSICAL (populations then hold f^eq(rho, u)) when psi^2 < 0 or
+ * rho <= 0 somewhere, LBM_ERR_OOM when the temporary copy cannot be made. */
+int lbm_axi_init_physical(lbm_axi* h, const double* rho, const double* u_z, const double* u_r);
+
+/* Same as lbm_axi_init_physical with device arrays (nz*nr doubles,
+ * [j*nz + k]); no allocation. */
+int lbm_axi_init_physical_device(lbm_axi* h, const double* d_rho, const double* d_u_z, const double* d_u_r);
+
 /* Advance n >= 0 time steps: gather (pull streaming with the boundary rules),
  * moments, psi, F = F_K + F_axis (+ rho g_z), EDM + BGK collision with the
  * axisymmetric source.  Waits for the stream and returns LBM_ERR_UNPHYSICAL

@@ -175,6 +175,19 @@ int read_error(lbm_axi* h) {
     return *h->herr ? LBM_ERR_UNPHYSICAL : LBM_OK;
 }
 
+// Bare velocity of a state whose physical velocity is to be u:
+// the solve holds f^eq(rho, u) and (pz, pr) its physical velocity
+// u + F/(2 rho), so u0 = u - F/(2 rho) = 2 u - (pz, pr), written over (pz, pr).
+__global__ void __launch_bounds__(256) k_bare_from_physical(long long n, const double* __restrict__ uz,
+                                                           const double* __restrict__ ur, double* __restrict__ pz,
+                                                           double* __restrict__ pr) {
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const double vz = uz ? uz[c] : 0.0, vr = ur ? ur[c] : 0.0;
+    pz[c] = vz - (pz[c] - vz);
+    pr[c] = vr - (pr[c] - vr);
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -368,6 +381,48 @@ int lbm_axi_init(lbm_axi* h, const double* rho, const double* uz, const double* 
     if (e == cudaSuccess && ur) e = cudaMemcpyAsync(d_ur, ur, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return LBM_ERR_CUDA;
     return lbm_axi_init_device(h, d_rho, d_uz, d_ur);
+}
+
+int lbm_axi_init_physical_device(lbm_axi* h, const double* rho, const double* uz, const double* ur) {
+    int rc = lbm_axi_init_device(h, rho, uz, ur);
+    if (rc != LBM_OK) return rc;
+    DeviceGuard g(h->device);
+    const long long n = (long long)h->nz * h->nr;
+    cudaError_t e = enqueue_density(h);
+    if (e == cudaSuccess) {
+        if (h->precision == 32)
+            e = Ops<float>::moments(h->pf, h->pdd, (const float*)h->f[h->cur], (const float*)h->aux, h->mout,
+                                    h->stream);
+        else
+            e = Ops<double>::moments(h->pdd, h->pdd, (const double*)h->f[h->cur], (const double*)h->aux, h->mout,
+                                     h->stream);
+    }
+    if (e == cudaSuccess) {
+        k_bare_from_physical<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(n, uz, ur, h->mout + n,
+                                                                                   h->mout + 2 * n);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    rc = read_error(h);
+    if (rc != LBM_OK) return rc;
+    return lbm_axi_init_device(h, rho, h->mout + n, h->mout + 2 * n);
+}
+
+int lbm_axi_init_physical(lbm_axi* h, const double* rho, const double* uz, const double* ur) {
+    if (!h || !rho) return LBM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    const size_t n = (size_t)h->nz * h->nr;
+    double* d = nullptr;
+    if (cudaMalloc(&d, 3 * n * sizeof(double)) != cudaSuccess) return LBM_ERR_OOM;
+    cudaError_t e = cudaMemcpyAsync(d, rho, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && uz) e = cudaMemcpyAsync(d + n, uz, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && ur)
+        e = cudaMemcpyAsync(d + 2 * n, ur, n * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    int rc = e == cudaSuccess ? lbm_axi_init_physical_device(h, d, uz ? d + n : nullptr, ur ? d + 2 * n : nullptr)
+                              : LBM_ERR_CUDA;
+    cudaStreamSynchronize(h->stream);
+    cudaFree(d);
+    return rc;
 }
 
 int lbm_axi_step_async(lbm_axi* h, long long n) {

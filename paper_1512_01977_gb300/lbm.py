@@ -60,6 +60,8 @@ _SIGS = {
                                  C.POINTER(lbm_axi_opts), C.POINTER(_H)]),
     "lbm_axi_init": (C.c_int, [_H, _D, _D, _D]),
     "lbm_axi_init_device": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "lbm_axi_init_physical": (C.c_int, [_H, _D, _D, _D]),
+    "lbm_axi_init_physical_device": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_axi_step": (C.c_int, [_H, C.c_longlong]),
     "lbm_axi_step_async": (C.c_int, [_H, C.c_longlong]),
     "lbm_axi_sync": (C.c_int, [_H]),
@@ -183,6 +185,17 @@ def lbm_axi_init(h, nz, nr, rho, u_z=None, u_r=None):
 
 def lbm_axi_init_device(h, rho, u_z=None, u_r=None):
     _check(lib().lbm_axi_init_device(h, _devptr(rho), _devptr(u_z), _devptr(u_r)), "lbm_axi_init_device")
+
+
+def lbm_axi_init_physical(h, nz, nr, rho, u_z=None, u_r=None):
+    n = nz * nr
+    rho, u_z, u_r = _host(rho, n), _host(u_z, n), _host(u_r, n)
+    _check(lib().lbm_axi_init_physical(h, _dptr(rho), _dptr(u_z), _dptr(u_r)), "lbm_axi_init_physical")
+
+
+def lbm_axi_init_physical_device(h, rho, u_z=None, u_r=None):
+    _check(lib().lbm_axi_init_physical_device(h, _devptr(rho), _devptr(u_z), _devptr(u_r)),
+           "lbm_axi_init_physical_device")
 
 
 def lbm_axi_step(h, n):
@@ -428,8 +441,10 @@ class Solver:
         self.eos = eos
         self.h = lbm_axi_create(nz, nr, tau, eos, A, o)
 
-    def init(self, rho, u_z=None, u_r=None):
-        lbm_axi_init(self.h, self.nz, self.nr, rho, u_z, u_r)
+    def init(self, rho, u_z=None, u_r=None, physical=False):
+        """f = f^eq: u is the bare velocity, or with physical=True the fluid
+        velocity u0 + F/(2 rho) (at rest for u = 0)."""
+        (lbm_axi_init_physical if physical else lbm_axi_init)(self.h, self.nz, self.nr, rho, u_z, u_r)
         return self
 
     def step(self, n=1):

@@ -107,3 +107,21 @@ def test_full_size_wave_sampled_windows(n_steps):
         r = {k: mo[k][inner] for k in ("rho", "uz", "ur", "p")}
         assert rel_err(g["rho"], r["rho"]) <= 1e-6
         assert vel_err(g, r) <= 1e-4
+
+
+def test_oscillation_settings_from_rest_fp32():
+    """The oscillating-droplet settings (vdW, T = 0.8 T_c, A = 0, tau = 0.7),
+    started at rest, in FP32 (rho_ref = rho_v) against the oracle: same bars
+    as the CS droplet."""
+    c = Case(64, 48, tau=0.7, eos=O.EOS_VDW, A=0.0, T_over_Tc=0.8)
+    rv, rl = c.coexistence()
+    fields = I.ellipsoid(64, 48, 14, 17, rl, rv)
+    o = O.Oracle(c.oracle_params()).init(*fields, physical=True).step(1500)
+    s = c.solver(precision=32, rho_ref=rv).init(*fields, physical=True).step(1500)
+    mo, mg = o.moments(), s.moments()
+    mr, _ = s.mass()
+    s.close()
+    e = {"rho": rel_err(mg["rho"], mo["rho"]), "u": vel_err(mg, mo), "p": rel_err(mg["p"], mo["p"]),
+         "mass": abs(mr / o.mass_rweighted() - 1)}
+    print("FP32 oscillation-settings errors", e)
+    assert e["rho"] <= 2e-4 and e["u"] <= 1e-3 and e["p"] <= 1e-3 and e["mass"] <= 2e-5, e

@@ -238,3 +238,48 @@ def test_device_init_and_moments():
     for k, t in zip(("rho", "uz", "ur", "p"), out):
         np.testing.assert_array_equal(t.cpu().numpy().reshape(24, 40), host[k])
     s.close()
+
+
+@pytest.mark.parametrize("device_arrays", [False, True])
+def test_init_physical_fp64(device_arrays):
+    """lbm_axi_init_physical(_device): the first state's fluid velocity is the
+    given u (the droplet starts at rest plus a random flow), equal to the
+    oracle's start, and a run from it at the oscillating-droplet settings
+    (vdW, T = 0.8 T_c, A = 0, tau = 0.7) follows the oracle."""
+    import torch
+
+    from paper_1512_01977_gb300 import lbm
+
+    c = Case(45, 27, tau=0.7, eos=O.EOS_VDW, A=0.0, T_over_Tc=0.8)
+    fields = _droplet_fields(c, 10, du=2e-3, seed=12)
+    o = O.Oracle(c.oracle_params()).init(*fields, physical=True)
+    mo0 = o.moments()
+    s = c.solver()
+    if device_arrays:
+        d = [torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda") for a in fields]
+        lbm.lbm_axi_init_physical_device(s.h, *d)
+    else:
+        s.init(*fields, physical=True)
+    m0 = s.moments()
+    assert vel_err(m0, mo0) <= 1e-13
+    assert vel_err(m0, {"uz": fields[1], "ur": fields[2]}) <= 1e-13
+    assert rel_err(m0["rho"], mo0["rho"]) <= 1e-15
+    o.step(150)
+    s.step(150)
+    mo, mg = o.moments(), s.moments()
+    s.close()
+    assert rel_err(mg["rho"], mo["rho"]) <= TOL64 and vel_err(mg, mo) <= TOL64 and rel_err(mg["p"], mo["p"]) <= TOL64
+
+
+def test_init_physical_reports_unphysical_density():
+    from paper_1512_01977_gb300 import lbm
+
+    c = Case(16, 8)
+    rho = np.full((8, 16), 0.2)
+    rho[3, 5] = -0.1
+    s = c.solver()
+    with pytest.raises(lbm.LbmError) as e:
+        s.init(rho, physical=True)
+    assert e.value.code == lbm.ERR_UNPHYSICAL
+    s.init(np.full((8, 16), 0.2), physical=True).step(3)
+    s.close()
