@@ -330,7 +330,7 @@ def run_ours(args):
 def run_batched(args):
     """256 independent droplets (sizes log-uniform 64x32 .. 512x256, R = 0.25 of
     the shorter side, T/Tc ~ U[0.5, 0.85], tau ~ U[0.6, 1.0], CS, FP32 with
-    deviations about rho_v), `--steps` steps each: one batched launch per step
+    deviations about rho_v, started at rest), `--steps` steps each: one batched launch per step
     (autotuned) against the same solves stepped one at a time."""
     import torch
 
@@ -350,7 +350,7 @@ def run_batched(args):
             eos = lbm.make_eos(lbm.EOS_CS, sp["T_over_Tc"])
             rv, rl = lbm.lbm_eos_coexistence(eos)
             s = lbm.Solver(sp["nz"], sp["nr"], sp["tau"], eos=eos, A=A, precision=32, rho_ref=rv)
-            s.init(*I.droplet(sp["nz"], sp["nr"], sp["R"], rl, rv))
+            s.init(*I.droplet(sp["nz"], sp["nr"], sp["R"], rl, rv), physical=True)  # at rest
             out.append(s)
         return out
 

@@ -46,7 +46,8 @@ class Result:
 def make_solver(req, precision=32, stream=None):
     """Solver and initial fields of one request.  Droplets: P2-perturbed (0.05)
     droplet of radius 0.25 of the shorter side on the axis; waves:
-    rho0 (1 + 0.01 sin(2 pi z / nz)) + U(-1e-4, 1e-4) on the liquid branch."""
+    rho0 (1 + 0.01 sin(2 pi z / nz)) + U(-1e-4, 1e-4) on the liquid branch.
+    tau is the request's "tau" when given, else TAU."""
     kind = lbm.EOS_CS if req["eos"] == "cs" else lbm.EOS_VDW
     eos = lbm.make_eos(kind, req["T_over_Tc"], lam=LAMBDA_VDW)
     rv, rl = lbm.lbm_eos_coexistence(eos)
@@ -57,9 +58,16 @@ def make_solver(req, precision=32, stream=None):
     else:
         fields = I.density_wave(nz, nr, rl, seed=1000 + req["id"])
         rho_ref = rl
-    s = lbm.Solver(nz, nr, TAU, eos=eos, A=A, precision=precision, rho_ref=rho_ref if precision == 32 else 0.0,
+    s = lbm.Solver(nz, nr, req.get("tau", TAU), eos=eos, A=A, precision=precision, rho_ref=rho_ref if precision == 32 else 0.0,
                    stream=stream)
     return s, fields
+
+
+def start(s, fields):
+    """Initialise a request's solve with the fluid at rest (the given u = 0 is
+    the physical velocity), as the droplet tests of the method start."""
+    s.init(*fields, physical=True)
+    return s
 
 
 def _finish(s, req, status, t_arrive, t_start, t_done, keep_rho):
@@ -97,11 +105,18 @@ def serve(requests, budget_bytes=4 << 30, max_tick_steps=2000, precision=32, kee
             if active and used + fp > budget_bytes:
                 break
             s, fields = make_solver(req, precision)
-            s.init(*fields)
+            qi += 1
+            try:
+                start(s, fields)
+            except lbm.LbmError as e:  # unphysical initial state: retired at admission
+                t = clock() - t0
+                results.append(_finish(s, req, e.code, req["t_arrive"], t, t, keep_rho))
+                continue
             active.append(dict(req=req, s=s, remaining=req["steps"], t_start=clock() - t0, fp=fp))
             used += fp
-            qi += 1
         if not active:
+            if qi >= len(pending):
+                break
             # idle until the next arrival
             wait = pending[qi]["t_arrive"] - (clock() - t0)
             if wait > 0:
@@ -155,8 +170,8 @@ def serve_sequential(requests, precision=32, keep_rho=False, clock=None):
             time.sleep(req["t_arrive"] - now)
         t_start = clock() - t0
         s, fields = make_solver(req, precision)
-        s.init(*fields)
         try:
+            start(s, fields)
             s.step(req["steps"])
             st = lbm.OK
         except lbm.LbmError as e:

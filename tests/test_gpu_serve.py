@@ -26,9 +26,11 @@ def _requests():
     specs = [("droplet", "cs", 64, 48, 300, 0.85), ("wave", "vdw", 96, 32, 500, 0.8),
              ("droplet", "vdw", 80, 40, 200, 0.85), ("wave", "cs", 48, 64, 400, 0.9),
              ("droplet", "cs", 120, 60, 350, 0.88), ("wave", "cs", 40, 32, 150, 0.7),
-             ("droplet", "cs", 64, 40, 250, 0.5)]  # the last one is expected to go unphysical
-    return [dict(id=i, t_arrive=0.002 * i, kind=k, eos=e, nz=nz, nr=nr, steps=st, T_over_Tc=T)
+             ("droplet", "cs", 64, 40, 250, 0.5)]
+    reqs = [dict(id=i, t_arrive=0.002 * i, kind=k, eos=e, nz=nz, nr=nr, steps=st, T_over_Tc=T)
             for i, (k, e, nz, nr, st, T) in enumerate(specs)]
+    reqs[-1]["tau"] = 0.55  # ratio 725 at tau 0.55: expected to go unphysical
+    return reqs
 
 
 def test_served_results_equal_alone(env):
@@ -39,7 +41,7 @@ def test_served_results_equal_alone(env):
     by_id = {r.id: r for r in res}
     for req in reqs:
         s, fields = serve.make_solver(req)
-        s.init(*fields)
+        serve.start(s, fields)
         try:
             s.step(req["steps"])
             st = lbm.OK
@@ -68,3 +70,29 @@ def test_budget_bounds_resident_footprint(env):
     order = sorted(res, key=lambda r: r.t_start)
     for i in range(2, len(order)):
         assert order[i].t_start >= min(o.t_done for o in order[:i]) - 1e-9
+
+
+def test_unphysical_initial_state_is_retired_at_admission(env):
+    """A request whose initial density has psi^2 = rho/3 - P_k < 0 (a CS
+    liquid at twice rho_l) is retired with its error when admitted; the
+    others run."""
+    lbm, serve = env
+    reqs = [r for r in _requests() if r["id"] in (0, 1)]
+    bad = dict(reqs[0], id=9, t_arrive=0.0)
+    orig = serve.make_solver
+
+    def make(req, precision=32, stream=None):
+        s, fields = orig(req, precision, stream)
+        if req["id"] == 9:
+            fields = (fields[0] * 2.0,) + tuple(fields[1:])  # liquid at 2 rho_l: psi^2 < 0
+        return s, fields
+
+    serve.make_solver = make
+    try:
+        res, stats = serve.serve(reqs + [bad], max_tick_steps=64)
+    finally:
+        serve.make_solver = orig
+    by_id = {r.id: r for r in res}
+    assert by_id[9].status == lbm.ERR_UNPHYSICAL
+    assert by_id[0].status == lbm.OK and by_id[1].status == lbm.OK
+    assert stats["requests"] == 3
