@@ -14,6 +14,7 @@ Q = 9
 TOP_FREESLIP, TOP_NOSLIP, TOP_PERIODIC = 0, 1, 2
 EOS_VDW, EOS_CS = 0, 1
 KAPPA_THERMO, KAPPA_LATTICE, KAPPA_MIXED = 0, 1, 2
+H_LOCAL, H_LINK_AVG = 0, 1
 ERR_UNPHYSICAL = -4
 
 
@@ -23,7 +24,7 @@ class _CParams(C.Structure):
         ("eos", C.c_int), ("T", C.c_double), ("a", C.c_double), ("b", C.c_double),
         ("R", C.c_double), ("lam", C.c_double), ("top", C.c_int), ("axis", C.c_int),
         ("multiphase", C.c_int), ("kappa", C.c_int), ("hr_sign", C.c_int), ("gz", C.c_double),
-        ("r0", C.c_double),
+        ("r0", C.c_double), ("h_eval", C.c_int),
     ]
 
 
@@ -48,6 +49,7 @@ class Params:
     hr_sign: int = -1
     gz: float = 0.0
     r0: float = 0.0
+    h_eval: int = H_LOCAL
 
     def replace(self, **kw):
         return dataclasses.replace(self, **kw)

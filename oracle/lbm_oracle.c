@@ -36,6 +36,7 @@ static const double orc_w[ORC_Q] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.
 enum { ORC_TOP_FREESLIP = 0, ORC_TOP_NOSLIP = 1, ORC_TOP_PERIODIC = 2 };
 enum { ORC_EOS_VDW = 0, ORC_EOS_CS = 1 };
 enum { ORC_KAPPA_THERMO = 0, ORC_KAPPA_LATTICE = 1, ORC_KAPPA_MIXED = 2 };
+enum { ORC_H_LOCAL = 0, ORC_H_LINK_AVG = 1 };
 enum { ORC_OK = 0, ORC_ERR_UNPHYSICAL = -4 };
 
 typedef struct {
@@ -54,6 +55,7 @@ typedef struct {
     double gz;      /* constant body acceleration along z (0 for the paper's runs) */
     double r0;      /* row j sits at r = r0 + j + 1/2; 0 for a lattice that starts at the
                        axis.  r0 > 0 describes a window cut out of a larger lattice (tests). */
+    int h_eval;     /* where h_i of Eq. (lbm) is evaluated: ORC_H_LOCAL or ORC_H_LINK_AVG */
 } orc_params;
 
 /* ------------------------------------------------------------------ EOS -- */
@@ -426,6 +428,8 @@ static void orc_collide(const orc_params* P, const double* f, orc_work* w) {
             orc_feq(rho, w->u0z[e] + w->Fz[e] / rho, w->u0r[e] + w->Fr[e] / rho, feq1);
             if (P->axis) {
                 orc_source_h(r, rho, w->ur[e], w->Hz[e], w->Hr[e], h);
+                if (P->h_eval == ORC_H_LINK_AVG)
+                    for (int i = 0; i < ORC_Q; i++) h[i] *= 0.5; /* departure half, see orc_arrival_half */
             } else {
                 for (int i = 0; i < ORC_Q; i++) h[i] = 0.0;
             }
@@ -433,6 +437,28 @@ static void orc_collide(const orc_params* P, const double* f, orc_work* w) {
                 long c = i * n + (long)j * P->nz + k;
                 w->fpost[c] = f[c] + (feq0[i] - f[c]) / P->tau + (feq1[i] - feq0[i]) + h[i];
             }
+        }
+    }
+}
+
+/* h_i at the midpoint x + c_i/2 of the link, Eq. (lbm), read as the mean of
+ * its two end nodes at time t (ORC_H_LINK_AVG): the population leaving x
+ * carries h_i(x)/2 from the collision and receives h_i(y)/2 on arrival at y.
+ * After a boundary rule the arrival term is that of the direction and node
+ * the population arrives with; at the axis and at a free-slip top this is
+ * the h_i of the mirror ghost node for the original direction, because
+ * -rho u_r/r and H_z are even and H_r odd under r -> -r, u_r -> -u_r; at a
+ * no-slip top (bounce-back) it is the reversed direction's h_i at the same node.
+ * Called after streaming, with the fields of the step that just collided. */
+static void orc_arrival_half(const orc_params* P, const orc_work* w, double* f) {
+    long n = (long)P->nz * P->nr;
+    for (int j = 0; j < P->nr; j++) {
+        double r = P->r0 + j + 0.5;
+        for (int k = 0; k < P->nz; k++) {
+            long e = orc_ext(P, k, j);
+            double h[ORC_Q];
+            orc_source_h(r, w->rho[e], w->ur[e], w->Hz[e], w->Hr[e], h);
+            for (int i = 0; i < ORC_Q; i++) f[i * n + (long)j * P->nz + k] += 0.5 * h[i];
         }
     }
 }
@@ -450,6 +476,7 @@ int orc_run(const orc_params* P, double* f, long nsteps) {
         if (rc != ORC_OK) break;
         orc_collide(P, f, &w);
         orc_stream(P, w.fpost, f);
+        if (P->axis && P->h_eval == ORC_H_LINK_AVG) orc_arrival_half(P, &w, f);
     }
     orc_work_free(&w);
     return rc;
