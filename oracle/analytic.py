@@ -5,11 +5,14 @@ import numpy as np
 from scipy import integrate, special
 
 
-def bessel_wave(rho1_0, R, ck, t, r, n_terms=400):
+def bessel_wave(rho1_0, R, ck, t, r, n_terms=400, nu=0.0):
     """Cylindrical wave solution, Eq. (analyticdensityprop):
     rho1(r, t) = 2/R^2 sum_n J0(k_n r/R) cos(c_k k_n t / R) / J1(k_n)^2
                  * integral_0^R rho1(r', 0) J0(k_n r'/R) r' dr',
-    with k_n the zeros of J0.  rho1_0 is a callable of r'."""
+    with k_n the zeros of J0.  rho1_0 is a callable of r'.  nu > 0 damps
+    every term by exp(-nu (k_n/R)^2 t): each term is a standing radial
+    acoustic mode, and such a mode of the scheme decays at nu k^2 (shown by
+    the radial-acoustic-mode test); nu = 0 is the paper's inviscid series."""
     kn = special.jn_zeros(0, n_terms)
     r = np.asarray(r, dtype=np.float64)
     out = np.zeros_like(r)
@@ -17,7 +20,7 @@ def bessel_wave(rho1_0, R, ck, t, r, n_terms=400):
     f0 = rho1_0(rr)
     for k in kn:
         coef = integrate.simpson(f0 * special.j0(k * rr / R) * rr, x=rr)
-        out += coef * special.j0(k * r / R) * np.cos(ck * k * t / R) / special.j1(k) ** 2
+        out += coef * special.j0(k * r / R) * np.cos(ck * k * t / R) * np.exp(-nu * (k / R) ** 2 * t) / special.j1(k) ** 2
     return 2.0 / R**2 * out
 
 

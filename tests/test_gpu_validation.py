@@ -1,0 +1,272 @@
+"""The GPU path against the physics of Sec. III at the paper's scale.
+
+* Table 1: surface tension from the printed Young-Laplace law, Eq.
+  (laplacepressure), for an axisymmetric droplet and a fully periodic 2D
+  droplet (vdW, lambda = 0.01, R0 = 150, 500 x 200, tau = 1.5).
+* Young-Laplace for a sphere, dp = 2 sigma / R, over several radii.
+* The mode-2 oscillation of an ellipsoidal drop against the Miller-Scriven
+  frequency, Eq. (oscillatingfreq), for both readings of the c^4 factor of
+  F_axis, and its FP32 period error.
+* The radial density wave of Sec. III.C (1 x 2000, no-slip top) against the
+  Bessel series, Eq. (analyticdensityprop), in FP32, and against the oracle.
+
+Every test prints what it measured; the bars are stated in each test.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1512_01977_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+LAM = 0.01
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_01977_gb300 import build, lbm as L
+
+    build.build()
+    L.lib()
+    return L
+
+
+def _axis_state(rho):
+    """Equal-volume radius of an axisymmetric droplet centred on the axis,
+    with its inner (axis, centre) and outer (top corner) densities."""
+    nr, nz = rho.shape
+    rl, rv = rho[0, nz // 2], rho[-1, 0]
+    r = np.arange(nr) + 0.5
+    V = 2 * np.pi * np.sum(r[:, None] * (rho - rv) / (rl - rv))
+    return (3 * V / (4 * np.pi)) ** (1 / 3), rl, rv
+
+
+def _plane_state(rho):
+    n = rho.shape[0]
+    rl, rv = rho[n // 2, rho.shape[1] // 2], rho[0, 0]
+    return np.sqrt(np.sum((rho - rv) / (rl - rv)) / np.pi), rl, rv
+
+
+def _half_extent(row, rl, rv):
+    """Half the distance between the two crossings of (rho_l + rho_v)/2 on
+    the axis row (linear interpolation); nan if the liquid touches an end."""
+    mid = 0.5 * (rl + rv)
+    z = np.arange(len(row)) + 0.5
+    idx = np.nonzero(row > mid)[0]
+    if len(idx) == 0 or idx[0] == 0 or idx[-1] >= len(row) - 1:
+        return float("nan")
+    i0, i1 = idx[0], idx[-1]
+    zh = z[i1] + (mid - row[i1]) / (row[i1 + 1] - row[i1])
+    zl = z[i0 - 1] + (mid - row[i0 - 1]) / (row[i0] - row[i0 - 1])
+    return 0.5 * (zh - zl)
+
+
+# ------------------------------------------------------------- Table 1 --
+
+# Table 1 (sigma / lambda): (T, A) -> (2D, axis)
+TABLE1 = {(0.9, 0.0): (0.305, 0.304), (0.8, 0.0): (0.928, 0.928), (0.7, 0.0): (1.983, 2.009),
+          (0.9, -0.152): (0.371, 0.383), (0.8, -0.152): (1.146, 1.158), (0.7, -0.152): (2.285, 2.318)}
+
+
+def _laplace_printed(lbm, T, A, axis, steps=100000, R0=150):
+    """sigma / lambda = dp R / lambda (printed law) after `steps` steps, FP32,
+    with the outer average taken beyond R + 8 and beyond R + 24."""
+    eos = lbm.make_eos(lbm.EOS_VDW, T, lam=LAM)
+    rv, rl = lbm.lbm_eos_coexistence(eos)
+    if axis:
+        nz, nr = 500, 200
+        s = lbm.Solver(nz, nr, 1.5, eos=eos, A=A, precision=32, rho_ref=rv)
+        s.init(*I.droplet(nz, nr, R0, rl, rv, width=8.0), physical=True)
+    else:
+        nz = nr = 500
+        s = lbm.Solver(nz, nr, 1.5, eos=eos, A=A, precision=32, rho_ref=rv, top=lbm.TOP_PERIODIC, axis=0)
+        s.init(*I.droplet_2d(nz, nr, R0, rl, rv, width=8.0), physical=True)
+    s.step(steps)
+    rho = s.moments()["rho"]
+    R, _, _ = _axis_state(rho) if axis else _plane_state(rho)
+    rc = 0.0 if axis else nr / 2
+    out = [s.pressure_jump(nz / 2, rc, R / 2, R + gap) * R / LAM for gap in (8, 24)]
+    s.close()
+    return R, out
+
+
+@pytest.mark.parametrize("A", [0.0, -0.152])
+@pytest.mark.parametrize("T", [0.7, 0.8, 0.9])
+def test_table1_axis_vs_2d(lbm, T, A):
+    """Table 1's comparison at its own scale: with the paper's c_s -> c_k
+    substitution in F_axis (default), sigma from the printed law agrees
+    between the axisymmetric and the 2D droplet within the paper's 3.2 %.
+    The vapour average is taken beyond R + 24: at 0.9 T_c the interface is
+    wide enough that a shell at R + 8 still sits in its tail (ratio about
+    0.89 there).  The absolute values come out 1.5-1.9 times Table 1's."""
+    Ra, sa = _laplace_printed(lbm, T, A, True)
+    R2, s2 = _laplace_printed(lbm, T, A, False)
+    p2d, pax = TABLE1[(T, A)]
+    print("Table 1 T %.1f A %+.3f: axis R %.2f sigma/lam %.4f (R+24: %.4f) | 2D R %.2f sigma/lam %.4f (R+24: %.4f) | "
+          "ratio %.4f (R+24: %.4f) | paper 2D %.3f axis %.3f" % (T, A, Ra, sa[0], sa[1], R2, s2[0], s2[1],
+                                                                   sa[0] / s2[0], sa[1] / s2[1], p2d, pax))
+    assert sa[1] / s2[1] == pytest.approx(1.0, abs=0.032)
+
+
+# ---------------------------------------------------- Young-Laplace (1/R) --
+
+def test_young_laplace_sphere_over_radii(lbm):
+    """dp = 2 sigma / R for axisymmetric droplets of radius 32 .. 64 (CS,
+    T = 0.8 T_c, tau = 1, c_s^4 in F_axis): dp R is the same for every
+    radius within 6 %, and sigma = dp R / 2 is the planar droplet's within
+    10 %.  (A drop of radius 24 in its box evaporates into the vapour.)"""
+    eos = lbm.make_eos(lbm.EOS_CS, 0.8)
+    rv, rl = lbm.lbm_eos_coexistence(eos)
+    s = lbm.Solver(256, 256, 1.0, eos=eos, A=-0.152, precision=64, top=lbm.TOP_PERIODIC, axis=0)
+    s.init(*I.droplet_2d(256, 256, 48, rl, rv), physical=True)
+    s.step(20000)
+    R2, _, _ = _plane_state(s.moments()["rho"])
+    sig2d = s.pressure_jump(128, 128, R2 / 2, R2 + 12) * R2
+    s.close()
+    sig = []
+    for R0 in (32, 40, 48, 64):
+        nz, nr = 4 * R0 + 64, 2 * R0 + 48
+        s = lbm.Solver(nz, nr, 1.0, eos=eos, A=-0.152, precision=64, kappa=lbm.KAPPA_LATTICE)
+        s.init(*I.droplet(nz, nr, R0, rl, rv), physical=True)
+        s.step(20000)
+        R, _, _ = _axis_state(s.moments()["rho"])
+        sig.append(s.pressure_jump(nz / 2, 0, R / 2, R + 12) * R / 2)
+        s.close()
+    print("Young-Laplace sphere: sigma(R) =", np.round(sig, 6).tolist(), "sigma_2D = %.6f" % sig2d)
+    assert max(sig) / min(sig) < 1.06
+    for x in sig:
+        assert x == pytest.approx(sig2d, rel=0.10)
+
+
+# ----------------------------------------------------- mode-2 oscillation --
+
+def _oscillation(lbm, kappa, precision=64, shape=(62, 76), steps=25000, every=100):
+    """Mode-2 frequency of an ellipsoidal drop (CS, T = 0.8 T_c, A = -0.152,
+    tau = 1, 500 x 250, free-slip top) and the Miller-Scriven value for its
+    measured radius and densities, with sigma from a planar droplet."""
+    nz, nr, tau, A = 500, 250, 1.0, -0.152
+    eos = lbm.make_eos(lbm.EOS_CS, 0.8)
+    rv0, rl0 = lbm.lbm_eos_coexistence(eos)
+    # planar droplet: sigma of the scheme (no F_axis, so the same for both kappa readings)
+    s = lbm.Solver(320, 320, tau, eos=eos, A=A, precision=64, top=lbm.TOP_PERIODIC, axis=0)
+    s.init(*I.droplet_2d(320, 320, 64, rl0, rv0), physical=True)
+    s.step(30000)
+    R2, _, _ = _plane_state(s.moments()["rho"])
+    sig2d = s.pressure_jump(160, 160, R2 / 2, R2 + 12) * R2
+    s.close()
+    # the spherical drop of the same volume at rest: its equilibrium radius and densities
+    Ra, Rz = shape
+    R0 = (Ra * Ra * Rz) ** (1 / 3)
+    s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=64, kappa=kappa)
+    s.init(*I.droplet(nz, nr, R0, rl0, rv0), physical=True)
+    s.step(20000)
+    Rs, rl, rv = _axis_state(s.moments()["rho"])
+    s.close()
+    # the ellipsoid, scaled to that radius, at rest
+    k = Rs / R0
+    s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=precision, kappa=kappa,
+                   rho_ref=rv if precision == 32 else 0.0)
+    s.init(*I.ellipsoid(nz, nr, Ra * k, Rz * k, rl, rv), physical=True)
+    m_start = s.mass()[0]
+    ts, ext, rad, dens = [], [], [], []
+    for i in range(steps // every):
+        rho = lbm.lbm_axi_moments(s.h, nz, nr, want=("rho",))["rho"]
+        R, a, b = _axis_state(rho)
+        ts.append(i * every)
+        ext.append(_half_extent(rho[0], a, b))
+        rad.append(R)
+        dens.append((a, b))
+        s.step(every)
+    drift = s.mass()[0] / m_start - 1
+    s.close()
+    ts, ext = np.array(ts[3:]), np.array(ext[3:])
+    Rm = float(np.mean(rad[3:]))
+    rlm, rvm = np.mean([d[0] for d in dens[3:]]), np.mean([d[1] for d in dens[3:]])
+    nu = (tau - 0.5) / 3
+    w_ms = O.analytic.miller_scriven_omega2(sig2d, Rm, rlm, rvm, nu, nu)
+    w, c = O.analytic.fit_damped_cosine(ts, ext, w_guess=w_ms)
+    return dict(omega=w, decay=c, omega_ms=w_ms, err=w / w_ms - 1, R=Rm, sigma_2d=sig2d, mass_drift=drift,
+                ext=ext)
+
+
+def test_mode2_oscillation_lattice_kappa(lbm):
+    """With c_s^4 = 1/9 in F_axis the drop's mode-2 frequency is the
+    Miller-Scriven value within 5 % (the paper reports 6-8 % for its runs)."""
+    r = _oscillation(lbm, lbm.KAPPA_LATTICE)
+    print("mode 2, kappa c_s^4: omega %.4e MS %.4e err %+.4f R %.2f decay %.2e M_r drift %.1e"
+          % (r["omega"], r["omega_ms"], r["err"], r["R"], r["decay"], r["mass_drift"]))
+    assert abs(r["err"]) <= 0.05
+
+
+def test_mode2_oscillation_thermo_kappa(lbm):
+    """With the paper's c_s -> c_k substitution (c_k^4, default) the same
+    drop oscillates slower than Miller-Scriven: by 5-20 % here."""
+    r = _oscillation(lbm, lbm.KAPPA_THERMO)
+    print("mode 2, kappa c_k^4: omega %.4e MS %.4e err %+.4f R %.2f decay %.2e M_r drift %.1e"
+          % (r["omega"], r["omega_ms"], r["err"], r["R"], r["decay"], r["mass_drift"]))
+    assert -0.20 <= r["err"] <= -0.05
+
+
+def test_mode2_period_fp32(lbm):
+    """FP32 (deviations about rho_v) against FP64 for the same oscillation:
+    period within 1e-3, axis extent within 0.1 node, r-weighted mass drift
+    within 2e-4."""
+    r64 = _oscillation(lbm, lbm.KAPPA_LATTICE, precision=64, steps=15000)
+    r32 = _oscillation(lbm, lbm.KAPPA_LATTICE, precision=32, steps=15000)
+    dper = r64["omega"] / r32["omega"] - 1
+    dext = float(np.nanmax(np.abs(r64["ext"] - r32["ext"])))
+    print("mode 2 FP32 vs FP64: period error %.2e, max extent difference %.2e, M_r drift FP64 %.1e FP32 %.1e"
+          % (dper, dext, r64["mass_drift"], r32["mass_drift"]))
+    assert abs(dper) <= 1e-3 and dext <= 0.1 and abs(r32["mass_drift"]) <= 2e-4
+
+
+# -------------------------------------------------------- radial wave --
+
+def test_radial_density_wave_fp32(lbm):
+    """Sec. III.C at its scale (1 x 2000, vdW T = 0.8, lambda = 0.01,
+    rho0 = 1.8, A = 0, tau = 0.6, no-slip top) in FP32: a Gaussian ring
+    (w_d = 20, rho_p = 1e-3 rho0, centred at r = 120, started at rest)
+    splits into an inward and an outward wave.  Up to t_w = 3.98 they follow
+    the Bessel series, each mode damped at nu k^2, within 6 % of rho_p (the
+    inviscid series within 10 %); at t_w = 5 the inward wave focuses on the
+    axis (printed only).  FP32 (deviations about rho0) matches the FP64
+    oracle within 1e-2 rho_p (1e-5 of rho0; measured 1.3e-3 at t_w = 1
+    growing to 8e-3 as the wave focuses on the axis, where the 1/r terms
+    are largest) and keeps the r-weighted mass to 1e-7."""
+    nr, rho0, wd, rc = 2000, 1.8, 20.0, 120.0
+    rp = 1e-3 * rho0
+    p = O.Params(nz=1, nr=nr, tau=0.6, A=0.0, eos=O.EOS_VDW, T=0.8, lam=LAM, axis=1, top=O.TOP_NOSLIP)
+    ck = np.sqrt(O.eos.sound_speed_sq(p, rho0))
+    nu = (0.6 - 0.5) / 3
+    fields = I.radial_bump(1, nr, rho0, rp, wd, r_c=rc)
+    o = O.Oracle(p).init(*fields, physical=True)
+    eos = lbm.make_eos(lbm.EOS_VDW, 0.8, lam=LAM)
+    s = lbm.Solver(1, nr, 0.6, eos=eos, A=0.0, precision=32, rho_ref=rho0, top=lbm.TOP_NOSLIP)
+    s.init(*fields, physical=True)
+    m0 = s.mass()[0]
+    r = np.arange(nr) + 0.5
+    sel = slice(0, 400)
+    done = 0
+    for tw in (1.0, 2.0, 3.98, 5.0):
+        steps = int(round(tw * wd / ck))
+        o.step(steps - done)
+        s.step(steps - done)
+        done = steps
+        g = s.moments()["rho"][:, 0] - rho0
+        ref = o.moments()["rho"][:, 0] - rho0
+        bump = lambda x: rp * np.exp(-(((x - rc) / wd) ** 2))  # noqa: E731
+        e_vis = np.max(np.abs(g[sel] - O.analytic.bessel_wave(bump, nr, ck, steps, r[sel], 800, nu))) / rp
+        e_inv = np.max(np.abs(g[sel] - O.analytic.bessel_wave(bump, nr, ck, steps, r[sel], 800))) / rp
+        e_orc = np.max(np.abs(g - ref)) / rp
+        print("radial wave t_w %.2f: vs damped series %.3e, vs inviscid %.3e, FP32 vs oracle %.3e (of rho_p); "
+              "peak near the axis %.3f rho_p" % (tw, e_vis, e_inv, e_orc, g[:20].max() / rp))
+        assert e_orc <= 1e-2
+        if tw < 4:
+            assert e_vis <= 0.06 and e_inv <= 0.10
+    assert s.mass()[0] == pytest.approx(m0, rel=1e-7)
+    s.close()
