@@ -91,10 +91,10 @@ cudaError_t enqueue_step(lbm_axi* h) {
         const bool mp = h->opts.multiphase != 0, ax = h->opts.axis_terms != 0;
         if (h->precision == 32)
             e = Ops<float>::step_batch(static_cast<const lbm::BatchSolve<float>*>(h->d_self), h->d_self_start, 1,
-                                       mp, ax, c, 128, 0, h->derr, h->stream);
+                                       mp, ax, c, lbm::kStripWide, 0, h->derr, h->stream);
         else
             e = Ops<double>::step_batch(static_cast<const lbm::BatchSolve<double>*>(h->d_self), h->d_self_start,
-                                        1, mp, ax, c, 128, 0, h->derr, h->stream);
+                                        1, mp, ax, c, lbm::kStripWide, 0, h->derr, h->stream);
         h->cur = c ^ 1;
         return e;
     }
@@ -329,8 +329,8 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     *h->herr = 0;
     cudaError_t err = cudaSuccess;
     {
-        // descriptor of this solve for the batched kernel (strip width 128)
-        const long long start[2] = {0, (long long)((nz + 127) / 128) * nr};
+        // descriptor of this solve for the batched kernel (wide strips)
+        const long long start[2] = {0, (long long)((nz + lbm::kStripWide - 1) / lbm::kStripWide) * nr};
         if (o.precision == 32) {
             lbm::BatchSolve<float> d{h->pf, (const float*)h->f[0], (float*)h->f[1]};
             err = cudaMemcpy(h->d_self, &d, sizeof(d), cudaMemcpyHostToDevice);

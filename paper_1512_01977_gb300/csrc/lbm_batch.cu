@@ -182,7 +182,7 @@ int lbm_axi_batch_create(lbm_axi* const* solves, int n, void* stream, lbm_axi_ba
     b->stream = nullptr;
     b->own_stream = false;
     b->steps = 0;
-    b->strip = 128;
+    b->strip = lbm::kStripWide;
     b->grid = 0;
     b->graph = nullptr;
     b->graph_strip = b->graph_grid = -1;
@@ -312,7 +312,7 @@ int lbm_axi_batch_get_tuning(const lbm_axi_batch* b, lbm_axi_batch_tuning* t) {
 }
 
 int lbm_axi_batch_set_tuning(lbm_axi_batch* b, const lbm_axi_batch_tuning* t) {
-    if (!b || !t || (t->strip != 64 && t->strip != 128) || t->grid < 0) return LBM_ERR_INVALID_ARG;
+    if (!b || !t || (t->strip != lbm::kStripNarrow && t->strip != lbm::kStripWide) || t->grid < 0) return LBM_ERR_INVALID_ARG;
     DevGuard g(b->device);
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBM_ERR_CUDA;
     if (t->strip != b->strip) {
@@ -329,7 +329,7 @@ int lbm_axi_batch_autotune(lbm_axi_batch* b, int trials, lbm_axi_batch_tuning* c
     const int parity = (int)(b->steps & 1);
     float best = -1.f;
     lbm_axi_batch_tuning bt = {b->strip, b->grid};
-    const int strips[2] = {64, 128};
+    const int strips[2] = {lbm::kStripNarrow, lbm::kStripWide};
     for (int si = 0; si < 2; si++) {
         const int strip = strips[si];
         const int resident = b->precision == 32 ? Ops<float>::batch_resident_ctas(strip)

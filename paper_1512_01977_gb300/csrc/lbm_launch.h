@@ -10,6 +10,9 @@ namespace lbm {
 
 constexpr int kReduceBlocks = 304;  // 2 x 152 SMs; fixed so reductions are reproducible
 constexpr int kStepMinRows = 16;    // the single-pass kernel needs single reflections at the walls
+// z-columns per CTA of the two compiled forms of the batched kernel (the wide
+// one is the default; the autotuner may pick the narrow one for small grids).
+constexpr int kStripNarrow = 64, kStripWide = 96;
 
 template <typename R>
 struct Ops {

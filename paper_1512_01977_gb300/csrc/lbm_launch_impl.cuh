@@ -42,13 +42,14 @@ static cudaError_t launch_update(const Params<R>& p, const Params<double>& pd, c
 // Strip width and rows per iteration of the fused kernel per precision.
 template <typename R>
 struct StepTile;
+// CP: columns per thread (2: march2, pairs of nodes with packed FP32 arithmetic).
 template <>
 struct StepTile<float> {
-    static constexpr int TZ = 128, RR = 2, MINB = 3;  // 288 threads, 68.6 KB of rings
+    static constexpr int TZ = 96, RR = 2, CP = 2, MINB = 4;  // 128 threads, 45.8 KB of rings
 };
 template <>
 struct StepTile<double> {
-    static constexpr int TZ = 64, RR = 2, MINB = 2;  // 160 threads, 71.7 KB of rings
+    static constexpr int TZ = 64, RR = 2, CP = 1, MINB = 2;  // 160 threads, 71.7 KB of rings
 };
 
 template <typename R>
@@ -64,7 +65,7 @@ int Ops<R>::step_strip() {
 // The four compiled forms of the fused kernel (force on/off x axis terms on/off).
 template <typename R, bool MP, bool AX>
 static auto step_kernel() {
-    return k_step<R, StepTile<R>::TZ, StepTile<R>::RR, StepTile<R>::MINB, MP, AX>;
+    return k_step<R, StepTile<R>::TZ, StepTile<R>::RR, StepTile<R>::CP, StepTile<R>::MINB, MP, AX>;
 }
 
 template <typename R>
@@ -91,7 +92,7 @@ cudaError_t Ops<R>::prepare() {
     if (e == cudaSuccess) e = set_step_attr<R>((int)step_smem());
     // the batched kernel (also the default single-solve step): attributes and
     // occupancy are settled here, outside any stream capture
-    if (e == cudaSuccess && (batch_resident_ctas(64) <= 0 || batch_resident_ctas(128) <= 0))
+    if (e == cudaSuccess && (batch_resident_ctas(kStripNarrow) <= 0 || batch_resident_ctas(kStripWide) <= 0))
         e = cudaErrorInvalidConfiguration;
     return e;
 }
@@ -106,7 +107,7 @@ static int step_resident_ctas() {
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 152;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<R, true, true>(),
-                                                      StepShape<StepTile<R>::TZ, StepTile<R>::RR>::NT,
+                                                      StepShape<StepTile<R>::TZ, StepTile<R>::RR, StepTile<R>::CP>::NT,
                                                       Ops<R>::step_smem()) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
@@ -116,8 +117,8 @@ static int step_resident_ctas() {
 
 template <typename R>
 cudaError_t Ops<R>::step(const Params<R>& p, const R* f, R* fout, int rows_per_cta, int* err, cudaStream_t s) {
-    constexpr int TZ = StepTile<R>::TZ, RR = StepTile<R>::RR;
-    constexpr int NT = StepShape<TZ, RR>::NT;
+    constexpr int TZ = StepTile<R>::TZ, RR = StepTile<R>::RR, CP = StepTile<R>::CP;
+    constexpr int NT = StepShape<TZ, RR, CP>::NT;
     dim3 grid;
     if (rows_per_cta > 0) {
         grid = dim3((p.nz + TZ - 1) / TZ, (p.nr + rows_per_cta - 1) / rows_per_cta);
@@ -130,13 +131,13 @@ cudaError_t Ops<R>::step(const Params<R>& p, const R* f, R* fout, int rows_per_c
     }
     const size_t smem = step_smem();
     if (p.multiphase && p.axis)
-        k_step<R, TZ, RR, StepTile<R>::MINB, true, true><<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
+        step_kernel<R, true, true>()<<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
     else if (p.multiphase)
-        k_step<R, TZ, RR, StepTile<R>::MINB, true, false><<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
+        step_kernel<R, true, false>()<<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
     else if (p.axis)
-        k_step<R, TZ, RR, StepTile<R>::MINB, false, true><<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
+        step_kernel<R, false, true>()<<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
     else
-        k_step<R, TZ, RR, StepTile<R>::MINB, false, false><<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
+        step_kernel<R, false, false>()<<<grid, NT, smem, s>>>(p, f, fout, rows_per_cta, err);
     return cudaGetLastError();
 }
 
@@ -187,19 +188,28 @@ cudaError_t Ops<R>::pjump(const Params<R>& p, const Params<double>& pd, const R*
 
 namespace lbm {
 
-// Batched kernel forms: strip width 64 or 128 (the autotuner picks), force and
+// Batched kernel forms: strip width kStripNarrow or kStripWide (the autotuner picks), force and
 // axis terms compiled in or out.
+// Resident CTAs per SM the launch bounds ask for: what shared memory allows at
+// each width (FP32 two columns per thread: 45.8 KB / 31.5 KB of rings; FP64
+// one column: 91.6 KB / 63 KB).
+template <typename R, int TZ>
+struct BatchMinBlocks {
+    static constexpr int value = sizeof(R) == 4 ? (TZ == kStripWide ? 4 : 5) : (TZ == kStripWide ? 2 : 3);
+};
+
 template <typename R, int TZ>
 struct BatchTile {
     static constexpr int RR = 2;
-    static constexpr int MINB = TZ == 128 ? 3 : 5;
-    static constexpr int NT = StepShape<TZ, RR>::NT;
-    static size_t smem() { return sizeof(R) * (size_t)StepShape<TZ, RR>::elems; }
+    static constexpr int CP = StepTile<R>::CP;
+    static constexpr int MINB = BatchMinBlocks<R, TZ>::value;
+    static constexpr int NT = StepShape<TZ, RR, CP>::NT;
+    static size_t smem() { return sizeof(R) * (size_t)StepShape<TZ, RR, CP>::elems; }
 };
 
 template <typename R, int TZ, bool MP, bool AX>
 static auto batch_kernel() {
-    return k_step_batch<R, TZ, BatchTile<R, TZ>::RR, BatchTile<R, TZ>::MINB, MP, AX>;
+    return k_step_batch<R, TZ, BatchTile<R, TZ>::RR, BatchTile<R, TZ>::CP, BatchTile<R, TZ>::MINB, MP, AX>;
 }
 
 template <typename R, int TZ>
@@ -221,25 +231,25 @@ static cudaError_t batch_prepare() {
 
 template <typename R>
 size_t Ops<R>::batch_smem(int strip) {
-    return strip == 64 ? BatchTile<R, 64>::smem() : BatchTile<R, 128>::smem();
+    return strip == kStripNarrow ? BatchTile<R, kStripNarrow>::smem() : BatchTile<R, kStripWide>::smem();
 }
 
 template <typename R>
 int Ops<R>::batch_resident_ctas(int strip) {
     static int cached[2] = {0, 0};
-    const int slot = strip == 64 ? 0 : 1;
+    const int slot = strip == kStripNarrow ? 0 : 1;
     if (cached[slot] > 0) return cached[slot];
-    if ((strip == 64 ? batch_prepare<R, 64>() : batch_prepare<R, 128>()) != cudaSuccess) return 0;
+    if ((strip == kStripNarrow ? batch_prepare<R, kStripNarrow>() : batch_prepare<R, kStripWide>()) != cudaSuccess) return 0;
     int dev = 0, sms = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return 0;
-    cudaError_t e = strip == 64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                      &per_sm, batch_kernel<R, 64, true, true>(), BatchTile<R, 64>::NT,
-                                      BatchTile<R, 64>::smem())
+    cudaError_t e = strip == kStripNarrow ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                      &per_sm, batch_kernel<R, kStripNarrow, true, true>(), BatchTile<R, kStripNarrow>::NT,
+                                      BatchTile<R, kStripNarrow>::smem())
                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                      &per_sm, batch_kernel<R, 128, true, true>(), BatchTile<R, 128>::NT,
-                                      BatchTile<R, 128>::smem());
+                                      &per_sm, batch_kernel<R, kStripWide, true, true>(), BatchTile<R, kStripWide>::NT,
+                                      BatchTile<R, kStripWide>::smem());
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     cached[slot] = sms * per_sm;
     return cached[slot];
@@ -266,8 +276,8 @@ cudaError_t Ops<R>::step_batch(const BatchSolve<R>* solves, const long long* sta
                                int parity, int strip, int grid, int* err, cudaStream_t s) {
     if (grid <= 0) grid = batch_resident_ctas(strip);
     if (grid <= 0) return cudaErrorInvalidConfiguration;
-    return strip == 64 ? launch_batch<R, 64>(solves, start, n, mp, ax, parity, grid, err, s)
-                       : launch_batch<R, 128>(solves, start, n, mp, ax, parity, grid, err, s);
+    return strip == kStripNarrow ? launch_batch<R, kStripNarrow>(solves, start, n, mp, ax, parity, grid, err, s)
+                       : launch_batch<R, kStripWide>(solves, start, n, mp, ax, parity, grid, err, s);
 }
 
 }  // namespace lbm

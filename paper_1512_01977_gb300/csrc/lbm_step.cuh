@@ -105,15 +105,17 @@ __device__ __forceinline__ R fd_r_rows(const R* m2m, const R* mm, const R* mp, c
     return (R(8) * n1 - n2) * (R(1) / R(36));
 }
 
-template <int TZ, int RR>
+// CP = columns per thread (1: march, 2: march2).
+template <int TZ, int RR, int CP = 1>
 struct StepShape {
     static constexpr int LAG = RR + 2;
     static constexpr int WL = TZ + 12, WD = TZ + 8, WU = TZ + 4;
     // one item per thread in every stage (the widest, stage L, sets the count)
-    static constexpr int NT = (RR * WL + 31) / 32 * 32;
-    static constexpr int DP = 16, DD = 16, DJ = 16, DU = 8;  // ring depths (rows)
+    static constexpr int NT = (RR * WL / CP + 31) / 32 * 32;
+    // ring depths (rows), powers of two; schedule checked on the CPU for RR = 2 and 4
+    static constexpr int DP = RR <= 2 ? 16 : 32, DD = 16, DJ = RR <= 2 ? 16 : 32, DU = RR <= 2 ? 8 : 16;
     static constexpr int elems = DP * WL + 2 * DD * WD + 3 * DJ * WU + 2 * DU * WU;
-    // schedule constraints (checked exhaustively on the CPU for RR = 2)
+    // schedule constraints
     static_assert(11 + 2 * RR <= DP && 7 + 2 * RR <= DD && 6 + 4 * RR <= DJ && 4 + 2 * RR <= DU, "ring depth");
 };
 
@@ -375,19 +377,475 @@ __device__ __forceinline__ void march(const Params<R>& p, const R* __restrict__ 
     }
 }
 
+// ------------------------------------------------------- two columns each --
+// march2 runs the same stages, lags and rings as march, but every thread owns
+// two adjacent columns (c, c+1), c even, in every stage.  The index arithmetic,
+// bounds checks and ring addressing of an item serve two nodes; a quantity's
+// values at the two nodes travel as a pair that is loaded and stored as one
+// 2-wide access (ring widths and strip origins are even, so pairs are aligned)
+// and combined with the packed f32x2 instructions in FP32 (one issue for both
+// lanes).  A stencil over columns c-2 .. c+3 of a row is three aligned pairs.
+
+template <typename R>
+struct PairOf;
+template <>
+struct PairOf<float> {
+    using T = float2;
+};
+template <>
+struct PairOf<double> {
+    using T = double2;
+};
+
+__device__ __forceinline__ float2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 pk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+template <typename T, typename R>
+__device__ __forceinline__ T ld2(const R* a, int c) {
+    return *reinterpret_cast<const T*>(a + c);
+}
+template <typename T, typename R>
+__device__ __forceinline__ void st2(R* a, int c, T v) {
+    *reinterpret_cast<T*>(a + c) = v;
+}
+template <typename T>
+struct Tri {
+    T a, b, c;  // columns (c-2, c-1), (c, c+1), (c+2, c+3)
+};
+template <typename T, typename R>
+__device__ __forceinline__ Tri<T> ld3(const R* row, int c) {
+    return {ld2<T>(row, c - 2), ld2<T>(row, c), ld2<T>(row, c + 2)};
+}
+
+// fd_both for the nodes at columns c and c+1 (15 pair loads instead of 32).
+// Distance 1: n1z(k) = S(k+1) - S(k-1) with S the column sum of rows r-1..r+1,
+// n1r(k) = D(k-1) + D(k) + D(k+1) with D = row r+1 - row r-1.  Distance 2:
+// n2z = T(k+2) - T(k-2) with T the column sum of rows r-2, r, r+2, and
+// n2r = E(k-2) + E(k) + E(k+2) with E = row r+2 - row r-2: aligned pairs.
+template <typename R, typename T>
+__device__ __forceinline__ void fd_both2(const R* m2m, const R* mm, const R* m0, const R* mp, const R* m2p, int c,
+                                         T& dz, T& dr) {
+    const Tri<T> z0 = ld3<T>(m0, c), zm = ld3<T>(mm, c), zp = ld3<T>(mp, c);
+    const Tri<T> z2m = ld3<T>(m2m, c), z2p = ld3<T>(m2p, c);
+    const T Sa = padd(padd(z0.a, zp.a), zm.a), Sb = padd(padd(z0.b, zp.b), zm.b);
+    const T Sc = padd(padd(z0.c, zp.c), zm.c);
+    const T Da = psub(zp.a, zm.a), Db = psub(zp.b, zm.b), Dc = psub(zp.c, zm.c);
+    const R t = Db.x + Db.y;
+    const T n1z = pk(Sb.y - Sa.y, Sc.x - Sb.x);
+    const T n1r = pk(Da.y + t, Dc.x + t);
+    const T n2z = psub(padd(padd(z0.c, z2p.c), z2m.c), padd(padd(z0.a, z2p.a), z2m.a));
+    const T n2r = padd(padd(psub(z2p.a, z2m.a), psub(z2p.b, z2m.b)), psub(z2p.c, z2m.c));
+    const T k8 = pk(R(8) / R(36), R(8) / R(36)), k1 = pk(R(-1) / R(36), R(-1) / R(36));
+    dz = pfma(n1z, k8, pmul(n2z, k1));
+    dr = pfma(n1r, k8, pmul(n2r, k1));
+}
+// fd_r_rows for columns c and c+1 (12 pair loads instead of 24).
+template <typename R, typename T>
+__device__ __forceinline__ T fd_r2(const R* m2m, const R* mm, const R* mp, const R* m2p, int c) {
+    const Tri<T> zm = ld3<T>(mm, c), zp = ld3<T>(mp, c), z2m = ld3<T>(m2m, c), z2p = ld3<T>(m2p, c);
+    const T Da = psub(zp.a, zm.a), Db = psub(zp.b, zm.b), Dc = psub(zp.c, zm.c);
+    const R t = Db.x + Db.y;
+    const T n1 = pk(Da.y + t, Dc.x + t);
+    const T n2 = padd(padd(psub(z2p.a, z2m.a), psub(z2p.b, z2m.b)), psub(z2p.c, z2m.c));
+    const T k8 = pk(R(8) / R(36), R(8) / R(36)), k1 = pk(R(-1) / R(36), R(-1) / R(36));
+    return pfma(n1, k8, pmul(n2, k1));
+}
+// First moments of the Kupershtokh force for columns c and c+1 from psi (s1)
+// or psi^2 (s2) on rows r-1 (zm), r (z0), r+1 (zq):
+// sz(k) = V(k+1) - V(k-1), V = c9 row r + c36 (row r+1 + row r-1);
+// sr(k) = c9 D(k) + c36 (D(k-1) + D(k+1)), D = row r+1 - row r-1.
+template <typename R, typename T>
+__device__ __forceinline__ void kup_moments2(const Tri<T>& zm, const Tri<T>& z0, const Tri<T>& zq, T& sz, T& sr) {
+    const T c9 = pk(R(1) / R(9), R(1) / R(9)), c36 = pk(R(1) / R(36), R(1) / R(36));
+    const T Va = pfma(z0.a, c9, pmul(padd(zq.a, zm.a), c36));
+    const T Vb = pfma(z0.b, c9, pmul(padd(zq.b, zm.b), c36));
+    const T Vc = pfma(z0.c, c9, pmul(padd(zq.c, zm.c), c36));
+    sz = pk(Vb.y - Va.y, Vc.x - Vb.x);
+    const T Da = psub(zq.a, zm.a), Db = psub(zq.b, zm.b), Dc = psub(zq.c, zm.c);
+    sr = pfma(Db, c9, pmul(pk(Da.y + Db.y, Db.x + Dc.x), c36));
+}
+template <typename T>
+__device__ __forceinline__ Tri<T> sq3(const Tri<T>& z) {
+    return {pmul(z.a, z.a), pmul(z.b, z.b), pmul(z.c, z.c)};
+}
+
+template <typename R, typename T>
+__device__ __forceinline__ T prcp(T x) {
+    return pk(rcp<R>(x.x), rcp<R>(x.y));
+}
+// P_k and c_k^2 of a pair of densities (the formulas of eos_p_fast, eos_dp_fast).
+template <typename R, typename T>
+__device__ __forceinline__ T eos_p2(const Params<R>& p, T rho) {
+    const T one = pk(R(1), R(1));
+    if (p.eos == EOS_VDW) {
+        const T l8T = pk(R(8) * p.T * p.lambda, R(8) * p.T * p.lambda), l3 = pk(R(-3) * p.lambda, R(-3) * p.lambda);
+        const T d = psub(pk(R(3), R(3)), rho);
+        return pfma(pmul(rho, l8T), prcp<R>(d), pmul(pmul(rho, rho), l3));
+    }
+    const T e = pmul(rho, pk(p.b * R(0.25), p.b * R(0.25)));
+    const T om = psub(one, e);
+    const T num = pfma(e, pfma(e, om, one), one);
+    const T RT = pk(p.Rg * p.T, p.Rg * p.T), ma = pk(-p.a, -p.a);
+    return pfma(pmul(pmul(rho, RT), num), prcp<R>(pmul(pmul(om, om), om)), pmul(pmul(rho, rho), ma));
+}
+template <typename R, typename T>
+__device__ __forceinline__ T eos_dp2(const Params<R>& p, T rho) {
+    const T one = pk(R(1), R(1));
+    if (p.eos == EOS_VDW) {
+        const T d = psub(pk(R(3), R(3)), rho);
+        const T l24T = pk(R(24) * p.T * p.lambda, R(24) * p.T * p.lambda), l6 = pk(R(-6) * p.lambda, R(-6) * p.lambda);
+        return pfma(l24T, prcp<R>(pmul(d, d)), pmul(rho, l6));
+    }
+    const T e = pmul(rho, pk(p.b * R(0.25), p.b * R(0.25)));
+    const T om = psub(one, e);
+    const T om2 = pmul(om, om);
+    const T four = pk(R(4), R(4));
+    const T num = pfma(e, pfma(e, pfma(e, psub(e, four), four), four), one);
+    const T RT = pk(p.Rg * p.T, p.Rg * p.T), m2a = pk(R(-2) * p.a, R(-2) * p.a);
+    return pfma(pmul(RT, num), prcp<R>(pmul(om2, om2)), pmul(rho, m2a));
+}
+template <typename R, typename T>
+__device__ __forceinline__ T kappa2(const Params<R>& p, T rho) {
+    if (p.kappa == KAPPA_LATTICE) return pk(R(1) / R(9), R(1) / R(9));
+    const T c2 = eos_dp2<R>(p, rho);
+    return p.kappa == KAPPA_MIXED ? pmul(c2, pk(R(1) / R(3), R(1) / R(3))) : pmul(c2, c2);
+}
+
+// Pulled populations of nodes (k, j) and (k+1, j) (k, k+1 wrapped in z).
+// contig: columns k-1 .. k+2 need no wrap and k is even, so the second node's
+// slots follow the first's and the c_z = 0 directions load as aligned pairs.
+// LAST: the last read of these values in the step (stage C), loaded with the
+// evict-first streaming hint so that they do not displace lines still to be read.
+template <bool LAST, typename R, typename T>
+__device__ __forceinline__ void gather2(const Params<R>& p, const R* __restrict__ f, int j, int k, bool contig,
+                                        T (&fi)[Q]) {
+    if (contig && j >= 1 && j + 1 < p.nr) {
+        const int plane = (int)p.plane;
+        const R* b = f + j * p.pitch + k;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const R* q = b + i * plane - cr_of(i) * p.pitch - cz_of(i);
+            if (LAST) {
+                if (cz_of(i) == 0)
+                    fi[i] = __ldcs(reinterpret_cast<const T*>(q));
+                else
+                    fi[i] = pk(__ldcs(q), __ldcs(q + 1));
+            } else {
+                if (cz_of(i) == 0)
+                    fi[i] = ld2<T>(q, 0);
+                else
+                    fi[i] = pk(q[0], q[1]);
+            }
+        }
+    } else {
+        const int k1 = wrap_small(k + 1, p.nz);
+        const int kc0[3] = {wrap_small(k - 1, p.nz), k, k1};
+        const int kc1[3] = {k, k1, wrap_small(k1 + 1, p.nz)};
+        R a[Q], c[Q];
+        gather32(p, f, j, kc0, a);
+        gather32(p, f, j, kc1, c);
+#pragma unroll
+        for (int i = 0; i < Q; i++) fi[i] = pk(a[i], c[i]);
+    }
+}
+
+template <typename R, int TZ, int RR, bool MP, bool AX>
+__device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__ f, R* __restrict__ fout, int strip,
+                                       int j0, int jend, unsigned char* smem_raw, int& bad) {
+    using S = StepShape<TZ, RR, 2>;
+    using T = typename PairOf<R>::T;
+    constexpr int WL = S::WL, WD = S::WD, WU = S::WU, LAG = S::LAG;
+    constexpr int DP = S::DP, DD = S::DD, DJ = S::DJ, DU = S::DU;
+    constexpr int HL = WL / 2, HD = WD / 2, HU = WU / 2, HC = TZ / 2;  // pairs per row
+    R* sPsi = reinterpret_cast<R*>(smem_raw);  // [DP][WL]
+    R* sPz = sPsi + DP * WL;                   // [DD][WD]
+    R* sPr = sPz + DD * WD;
+    R* sRho = sPr + DD * WD;  // [DJ][WU]  rho - rho_ref
+    R* sJz = sRho + DJ * WU;
+    R* sJr = sJz + DJ * WU;
+    R* sUz = sJr + DJ * WU;  // [DU][WU]  physical velocity
+    R* sUr = sUz + DU * WU;
+
+    const int tid = threadIdx.x;
+    const int k0 = strip * TZ;
+    const int kn = min(TZ, p.nz - k0);
+    constexpr bool mp = MP, ax = AX;
+    // evict-first hints on stage C's loads (the last read of those populations
+    // in the step) and on the stores (read only in the next step, after the
+    // whole lattice has streamed through L2): measured ~1 % faster together
+    constexpr bool kStreamC = true, kStreamStore = true;
+    const bool periodic = p.top == TOP_PERIODIC;
+    const int nz = p.nz, nr = p.nr, pitch = p.pitch, plane = (int)p.plane;
+    const R rho_ref = p.rho_ref;
+
+    // Items: (row offset, first column of the pair); inactive items get a row
+    // offset far out of range.  Lane 1 of a pair may lie past the strip's
+    // last used column: it is computed (from in-range data) but never stored
+    // to global memory and raises no error bits.
+    constexpr int OFF = -100000;
+    const int lr = tid / HL, lc = 2 * (tid - (tid / HL) * HL);
+    const int l_rr = (tid < RR * HL && lc < kn + 12) ? lr : OFF;
+    const bool l_v1 = lc + 1 < kn + 12;
+    const int dr_ = tid / HD, dc = 2 * (tid - (tid / HD) * HD);
+    const int d_rr = (tid < RR * HD && dc < kn + 8) ? dr_ : OFF;
+    const int ur_ = tid / HU, uc = 2 * (tid - (tid / HU) * HU);
+    const int u_rr = (tid < RR * HU && uc < kn + 4) ? ur_ : OFF;
+    const int cr_ = tid / HC, cc = 2 * (tid - (tid / HC) * HC);
+    const int c_rr = (tid < RR * HC && cc < kn) ? cr_ : OFF;
+    const bool c_v1 = cc + 1 < kn;
+
+    const int lk = wrap_any(k0 - 6 + lc, nz);
+    const bool l_contig = lk >= 1 && lk + 2 < nz && (lk & 1) == 0;
+    const int ck = min(k0 + cc, nz - 1);
+    const bool c_contig = ck >= 1 && ck + 2 < nz && (ck & 1) == 0;
+
+    const R omega = p.tau_inv, om1 = R(1) - p.tau_inv;
+    const R kA = p.A, kB = R(1) - R(2) * p.A;
+    const R nu = p.nu, gz = p.gz, hrs = R(p.hr_sign);
+    const int uz_top = p.top == TOP_NOSLIP ? -1 : 1;
+
+    auto lsrc = [&](int row, int& sgn_r) {
+        int jm = row;
+        sgn_r = 1;
+        if (row < 0 || row >= nr) jm = map_row(p, row, -1, -1, sgn_r);
+        return jm;
+    };
+    auto l_valid = [&](int row) { return row >= j0 - 6 && row < jend + 6; };
+    auto c_valid = [&](int row) { return row >= j0 && row < jend; };
+
+    T lpf[Q], cpf[Q];  // populations gathered one iteration ahead (stage L, stage C)
+    {
+        int sg;
+        const int row = j0 - 6 + l_rr;
+        if (l_valid(row)) gather2<false>(p, f, lsrc(row, sg), lk, l_contig, lpf);
+        const int crw = j0 - 6 - 3 * LAG + c_rr;
+        if (c_valid(crw)) gather2<kStreamC>(p, f, crw, ck, c_contig, cpf);
+    }
+
+    for (int pb = j0 - 6; pb - 3 * LAG < jend; pb += RR) {
+        // ---- stage L: rho, j, psi of the prefetched populations.
+        {
+            const int row = pb + l_rr;
+            if (l_valid(row)) {
+                int sgn_r;
+                lsrc(row, sgn_r);
+                const T d1 = padd(padd(lpf[1], lpf[5]), lpf[7]), d2 = padd(padd(lpf[2], lpf[6]), lpf[8]);
+                const T drho = padd(padd(padd(lpf[0], lpf[3]), padd(lpf[4], d1)), d2);
+                const T jz = psub(d1, d2);
+                const T jr = psub(padd(padd(lpf[3], lpf[5]), lpf[8]), padd(padd(lpf[4], lpf[6]), lpf[7]));
+                const T rho = padd(drho, pk(rho_ref, rho_ref));
+                if (mp) {
+                    const T arg = psub(pmul(rho, pk(R(1) / R(3), R(1) / R(3))), eos_p2<R>(p, rho));
+                    if (!(arg.x >= R(0)) || (l_v1 && !(arg.y >= R(0)))) bad |= ERRBIT_PSI;
+                    st2(sPsi + (row & (DP - 1)) * WL, lc, pk(sqrt_nonneg(arg.x), sqrt_nonneg(arg.y)));
+                }
+                if (!(rho.x > R(0)) || (l_v1 && !(rho.y > R(0)))) bad |= ERRBIT_RHO;
+                const int cu = lc - 4;
+                if (cu >= 0 && cu < WU) {
+                    const int sj = (row & (DJ - 1)) * WU;
+                    st2(sRho + sj, cu, drho);
+                    st2(sJz + sj, cu, jz);
+                    st2(sJr + sj, cu, (periodic || sgn_r > 0) ? jr : psub(pk(R(0), R(0)), jr));
+                }
+            }
+            // issue the next iteration's gather now; it lands behind this iteration's arithmetic
+            int sg;
+            const int nrow = row + RR;
+            if (l_valid(nrow)) gather2<false>(p, f, lsrc(nrow, sg), lk, l_contig, lpf);
+        }
+
+        // ---- stage D: psi_z, psi_r (only with F_axis).
+        if (mp && ax) {
+            const int row = pb - LAG + d_rr;
+            if (row >= j0 - 4 && row < jend + 4) {
+                int er = row, s = 1;
+                if (!periodic && row >= nr) er = map_row(p, row, -1, -1, s);
+                T dz, dr;
+                fd_both2<R>(sPsi + ((er - 2) & (DP - 1)) * WL, sPsi + ((er - 1) & (DP - 1)) * WL,
+                            sPsi + (er & (DP - 1)) * WL, sPsi + ((er + 1) & (DP - 1)) * WL,
+                            sPsi + ((er + 2) & (DP - 1)) * WL, dc + 2, dz, dr);
+                const int o = (row & (DD - 1)) * WD;
+                st2(sPz + o, dc, dz);
+                st2(sPr + o, dc, s > 0 ? dr : psub(pk(R(0), R(0)), dr));
+            }
+        }
+
+        // ---- stage U: total force and physical velocity.
+        {
+            const int row = pb - 2 * LAG + u_rr;
+            if (row >= j0 - 2 && row < jend + 2) {
+                int er = row, s_ur = 1, s_uz = 1;
+                if (!periodic && row >= nr) {
+                    er = map_row(p, row, -1, -1, s_ur);
+                    s_uz = uz_top;
+                }
+                const int sj = (er & (DJ - 1)) * WU;
+                const T drho = ld2<T>(sRho + sj, uc);
+                const T rho = padd(drho, pk(rho_ref, rho_ref));
+                T fz = pmul(rho, pk(gz, gz)), fr = pk(R(0), R(0));
+                if (mp) {
+                    const int c = uc + 4;
+                    const Tri<T> z0 = ld3<T>(sPsi + (er & (DP - 1)) * WL, c);
+                    const Tri<T> zm = ld3<T>(sPsi + ((er - 1) & (DP - 1)) * WL, c);
+                    const Tri<T> zq = ld3<T>(sPsi + ((er + 1) & (DP - 1)) * WL, c);
+                    // Kupershtokh force, Eq. (kupershtokhforcing)
+                    T s1z, s1r, s2z, s2r;
+                    kup_moments2<R>(zm, z0, zq, s1z, s1r);
+                    kup_moments2<R>(sq3(zm), sq3(z0), sq3(zq), s2z, s2r);
+                    const T psi = z0.b;
+                    const T bk = pmul(pk(R(6) * kB, R(6) * kB), psi), a6k = pk(R(6) * kA, R(6) * kA);
+                    fz = pfma(a6k, s2z, pfma(bk, s1z, fz));
+                    fr = pfma(a6k, s2r, pfma(bk, s1r, fr));
+                    if (ax) {
+                        // F_axis, Eq. (multiphasecorrections); psi_rr = D_r(psi_r), psi_rz = D_r(psi_z)
+                        const int cd = uc + 2;
+                        const int o2m = ((er - 2) & (DD - 1)) * WD, o1m = ((er - 1) & (DD - 1)) * WD;
+                        const int o1p = ((er + 1) & (DD - 1)) * WD, o2p = ((er + 2) & (DD - 1)) * WD;
+                        const int o0 = (er & (DD - 1)) * WD;
+                        const T prr = fd_r2<R, T>(sPr + o2m, sPr + o1m, sPr + o1p, sPr + o2p, cd);
+                        const T prz = fd_r2<R, T>(sPz + o2m, sPz + o1m, sPz + o1p, sPz + o2p, cd);
+                        const T psz = ld2<T>(sPz + o0, cd), psr = ld2<T>(sPr + o0, cd);
+                        int rrow = er;
+                        if (periodic) rrow = row < 0 ? row + nr : (row >= nr ? row - nr : row);
+                        const R ir = rcp(R(rrow) + R(0.5));
+                        const T irr = pk(ir, ir);
+                        const T k3 = pmul(pk(R(3), R(3)), kappa2<R>(p, rho));
+                        const T a6 = pmul(pk(R(6) * kA * ir, R(6) * kA * ir), psr);
+                        const T pir = pmul(psi, irr);
+                        fz = pfma(k3, pfma(pir, prz, pmul(a6, psz)), fz);
+                        fr = pfma(k3, pfma(pir, psub(prr, pmul(psr, irr)), pmul(a6, psr)), fr);
+                    }
+                }
+                const T irho = prcp<R>(rho);
+                const T half = pk(R(0.5), R(0.5));
+                const int ou = (row & (DU - 1)) * WU;
+                const T vz = pmul(pfma(half, fz, ld2<T>(sJz + sj, uc)), irho);
+                const T vr = pmul(pfma(half, fr, ld2<T>(sJr + sj, uc)), irho);
+                st2(sUz + ou, uc, s_uz > 0 ? vz : psub(pk(R(0), R(0)), vz));
+                st2(sUr + ou, uc, s_ur > 0 ? vr : psub(pk(R(0), R(0)), vr));
+            }
+        }
+
+        // ---- stage C: collide and store.
+        {
+            const int row = pb - 3 * LAG + c_rr;
+            T fi[Q];
+#pragma unroll
+            for (int i = 0; i < Q; i++) fi[i] = cpf[i];
+            if (c_valid(row + RR)) gather2<kStreamC>(p, f, row + RR, ck, c_contig, cpf);  // next iteration's gather
+            if (c_valid(row)) {
+                const int c = cc + 2;
+                const int sj = (row & (DJ - 1)) * WU;
+                const T drho = ld2<T>(sRho + sj, c);
+                const T rho = padd(drho, pk(rho_ref, rho_ref));
+                const T irho = prcp<R>(rho);
+                const T u0z = pmul(ld2<T>(sJz + sj, c), irho), u0r = pmul(ld2<T>(sJr + sj, c), irho);
+                const int ou = (row & (DU - 1)) * WU;
+                const T uz = ld2<T>(sUz + ou, c), ur = ld2<T>(sUr + ou, c);
+                // EDM velocity shift F / rho from u = u0 + F / (2 rho)
+                const T two = pk(R(2), R(2));
+                const T u1z = pfma(two, psub(uz, u0z), u0z), u1r = pfma(two, psub(ur, u0r), u0r);
+                T Hz = pk(R(0), R(0)), Hr = Hz, m0 = Hz;
+                if (ax) {
+                    const int o2m = ((row - 2) & (DU - 1)) * WU, o1m = ((row - 1) & (DU - 1)) * WU;
+                    const int o1p = ((row + 1) & (DU - 1)) * WU, o2p = ((row + 2) & (DU - 1)) * WU;
+                    const T duz_dr = fd_r2<R, T>(sUz + o2m, sUz + o1m, sUz + o1p, sUz + o2p, c);
+                    T dur_dz, dur_dr;
+                    fd_both2<R>(sUr + o2m, sUr + o1m, sUr + ou, sUr + o1p, sUr + o2p, c, dur_dz, dur_dr);
+                    const R ir = rcp(R(row) + R(0.5));
+                    const T irr = pk(ir, ir);
+                    const T mu = pmul(rho, pk(nu, nu));
+                    const T rur = pmul(rho, ur);
+                    Hz = pmul(psub(pmul(mu, padd(duz_dr, dur_dz)), pmul(rur, uz)), irr);
+                    Hr = pmul(psub(pmul(pmul(pk(R(2), R(2)), mu), pfma(pk(hrs * ir, hrs * ir), ur, dur_dr)),
+                                   pmul(rur, ur)),
+                              irr);
+                    m0 = pmul(pk(-ir, -ir), rur);
+                }
+                // f*_i = (1 - omega) f_i + f^eq_i(u1) - (1 - omega) f^eq_i(u0) + h_i, opposite
+                // directions sharing the even part (see march)
+                const T om1p = pk(om1, om1), c15 = pk(R(1.5), R(1.5)), c45 = pk(R(4.5), R(4.5));
+                const T u0sq = pfma(u0z, u0z, pmul(u0r, u0r)), u1sq = pfma(u1z, u1z, pmul(u1r, u1r));
+                const T base = pfma(pk(omega, omega), drho, pmul(rho, pmul(c15, psub(pmul(om1p, u0sq), u1sq))));
+                R* o = fout + row * pitch + k0 + cc;
+                auto store = [&](int i, T v) {
+                    if (kStreamStore) {
+                        if (c_v1)
+                            __stcs(reinterpret_cast<T*>(o + i * plane), v);
+                        else
+                            __stcs(o + i * plane, v.x);
+                    } else {
+                        if (c_v1)
+                            st2(o + i * plane, 0, v);
+                        else
+                            o[i * plane] = v.x;
+                    }
+                };
+                store(0, pfma(om1p, fi[0], pmul(pk(w_of<R>(0), w_of<R>(0)), padd(base, m0))));
+#pragma unroll
+                for (int m = 0; m < 4; m++) {
+                    const int i = 2 * m + 1;  // i and i+1 are opposite
+                    const R w = w_of<R>(i);
+                    const int cx = cz_of(i), cy = cr_of(i);
+                    T cu0, cu1, cH;
+                    if (cy == 0) {
+                        cu0 = u0z, cu1 = u1z, cH = Hz;
+                    } else if (cx == 0) {
+                        cu0 = u0r, cu1 = u1r, cH = Hr;
+                    } else if (cx == cy) {
+                        cu0 = padd(u0z, u0r), cu1 = padd(u1z, u1r), cH = padd(Hz, Hr);
+                    } else {
+                        cu0 = psub(u0z, u0r), cu1 = psub(u1z, u1r), cH = psub(Hz, Hr);
+                    }
+                    if (cx + cy < 0) {  // the pair's first direction points to -z or -r: flip
+                        const T z = pk(R(0), R(0));
+                        cu0 = psub(z, cu0), cu1 = psub(z, cu1), cH = psub(z, cH);
+                    }
+                    const T even = pmul(pk(w, w), padd(padd(base, m0),
+                                                       pmul(rho, pmul(c45, psub(pmul(cu1, cu1),
+                                                                                pmul(om1p, pmul(cu0, cu0)))))));
+                    const T odd = pmul(pk(R(3) * w, R(3) * w), pfma(rho, psub(cu1, pmul(om1p, cu0)), cH));
+                    store(i, padd(pfma(om1p, fi[i], even), odd));
+                    store(i + 1, psub(pfma(om1p, fi[i + 1], even), odd));
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Grid: one CTA per resident slot.  The flattened strip-row space
 // (strip * nr + row) is cut into gridDim.x equal contiguous ranges; a CTA
 // marches each strip segment of its range (usually one or two).  rows_per_cta
 // > 0 instead gives fixed chunks: CTA (x, y) = strip x, rows [y R, y R + R).
-template <typename R, int TZ, int RR, int MINB, bool MP, bool AX>
-__global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB) k_step(Params<R> p, const R* __restrict__ f,
-                                                                      R* __restrict__ fout, int rows_per_cta,
-                                                                      int* __restrict__ err) {
+template <typename R, int TZ, int RR, int CP, bool MP, bool AX>
+__device__ __forceinline__ void march_cp(const Params<R>& p, const R* __restrict__ f, R* __restrict__ fout, int strip,
+                                         int j0, int jend, unsigned char* smem_raw, int& bad) {
+    if constexpr (CP == 2)
+        march2<R, TZ, RR, MP, AX>(p, f, fout, strip, j0, jend, smem_raw, bad);
+    else
+        march<R, TZ, RR, MP, AX>(p, f, fout, strip, j0, jend, smem_raw, bad);
+}
+
+template <typename R, int TZ, int RR, int CP, int MINB, bool MP, bool AX>
+__global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB) k_step(Params<R> p, const R* __restrict__ f,
+                                                                          R* __restrict__ fout, int rows_per_cta,
+                                                                          int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int bad = 0;
     if (rows_per_cta > 0) {
         const int j0 = blockIdx.y * rows_per_cta;
-        march<R, TZ, RR, MP, AX>(p, f, fout, blockIdx.x, j0, min(j0 + rows_per_cta, p.nr), smem_raw, bad);
+        march_cp<R, TZ, RR, CP, MP, AX>(p, f, fout, blockIdx.x, j0, min(j0 + rows_per_cta, p.nr), smem_raw, bad);
     } else {
         const int nstrips = (p.nz + TZ - 1) / TZ;
         const long long total = (long long)nstrips * p.nr;
@@ -397,7 +855,7 @@ __global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB) k_step(Params<R> 
         while (a < b) {
             const int strip = (int)(a / p.nr), j0 = (int)(a - (long long)strip * p.nr);
             const int jend = (int)min((long long)p.nr, j0 + (b - a));
-            march<R, TZ, RR, MP, AX>(p, f, fout, strip, j0, jend, smem_raw, bad);
+            march_cp<R, TZ, RR, CP, MP, AX>(p, f, fout, strip, j0, jend, smem_raw, bad);
             a += jend - j0;
         }
     }
@@ -410,8 +868,8 @@ __global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB) k_step(Params<R> 
 // one-wave grid cuts the concatenation into equal contiguous shares, and each
 // CTA marches the (solve, strip, rows) segments of its share.  Even batch
 // steps read f_a and write f_b, odd steps the reverse.
-template <typename R, int TZ, int RR, int MINB, bool MP, bool AX>
-__global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB)
+template <typename R, int TZ, int RR, int CP, int MINB, bool MP, bool AX>
+__global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB)
     k_step_batch(const BatchSolve<R>* __restrict__ solves, const long long* __restrict__ start, int nsolves,
                  int parity, int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -437,7 +895,7 @@ __global__ void __launch_bounds__(StepShape<TZ, RR>::NT, MINB)
         const R* fin = parity ? solves[s].f_b : solves[s].f_a;
         R* fo = parity ? const_cast<R*>(solves[s].f_a) : solves[s].f_b;
         int bad = 0;
-        march<R, TZ, RR, MP, AX>(sp, fin, fo, strip, j0, jend, smem_raw, bad);
+        march_cp<R, TZ, RR, CP, MP, AX>(sp, fin, fo, strip, j0, jend, smem_raw, bad);
         if (bad) atomicOr(&err[s], bad);
         a += jend - j0;
     }

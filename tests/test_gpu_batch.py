@@ -41,10 +41,10 @@ def _mix(seed=4, n=7, precision=64):
 
 
 @pytest.mark.parametrize("precision", [64, 32])
-@pytest.mark.parametrize("strip", [64, 128])
+@pytest.mark.parametrize("strip", [64, 96])
 def test_batch_equals_alone(lbm, precision, strip):
-    """Same kernel code alone (a batch of one, strip 128) and in the batch:
-    bitwise equal at strip 128; with strip 64 (another compiled form) FP32
+    """Same kernel code alone (a batch of one, strip 96) and in the batch:
+    bitwise equal at strip 96; with strip 64 (another compiled form) FP32
     may differ in the last bits (FMA contraction), bounded here by 1e-6."""
     mix = _mix(precision=precision)
     alone = []
@@ -60,7 +60,7 @@ def test_batch_equals_alone(lbm, precision, strip):
     assert b.status() == [lbm.OK] * len(solvers)
     for s, ref in zip(solvers, alone):
         m = s.moments()
-        if strip == 128 or precision == 64:
+        if strip == 96 or precision == 64:
             for k in ("rho", "uz", "ur", "p"):
                 np.testing.assert_array_equal(m[k], ref[k])
         else:
@@ -122,7 +122,7 @@ def test_autotuners_are_non_destructive(lbm):
     b = lbm.Batch(solvers)
     b.step(10)
     strip, grid = b.autotune(trials=3)
-    assert strip in (64, 128)
+    assert strip in (64, 96)
     b.step(15)
     for s, r in zip(solvers, ref):
         np.testing.assert_array_equal(s.moments()["rho"], r)

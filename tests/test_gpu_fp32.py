@@ -125,3 +125,25 @@ def test_oscillation_settings_from_rest_fp32():
          "mass": abs(mr / o.mass_rweighted() - 1)}
     print("FP32 oscillation-settings errors", e)
     assert e["rho"] <= 2e-4 and e["u"] <= 1e-3 and e["p"] <= 1e-3 and e["mass"] <= 2e-5, e
+
+
+def test_laplace_pressure_fp32():
+    """Young-Laplace pressure jump of a droplet (CS, T = 0.8 T_c, R = 24,
+    10000 steps from rest), FP32 (rho_ref = rho_v) against FP64: dp within
+    1e-2 relative (measured 2.7e-3), r-weighted mass drift within 5e-5 of
+    FP64's (measured FP32 1.5e-5 against FP64 -7.7e-7)."""
+    c = Case(160, 96)
+    rv, rl = c.coexistence()
+    fields = I.droplet(160, 96, 24, rl, rv)
+    out = {}
+    for prec in (64, 32):
+        s = c.solver(prec, rv if prec == 32 else 0.0).init(*fields, physical=True)
+        m0 = s.mass()[0]
+        s.step(10000)
+        out[prec] = (s.pressure_jump(80, 0, 12, 36), s.mass()[0] / m0 - 1)
+        s.close()
+    e_dp = abs(out[32][0] / out[64][0] - 1)
+    e_m = abs(out[32][1] - out[64][1])
+    print("FP32 Laplace: dp FP64 %.6e FP32 %.6e rel %.2e; M_r drift FP64 %.1e FP32 %.1e" %
+          (out[64][0], out[32][0], e_dp, out[64][1], out[32][1]))
+    assert e_dp <= 1e-2 and e_m <= 5e-5
