@@ -213,6 +213,23 @@ int lbm_axi_pressure_jump(lbm_axi* h, double z_c, double r_c, double r_in, doubl
 #define LBM_NOALLOC_MAX_NODES 8388608
 int lbm_axi_mass_field_noalloc(const double* d_rho, int nz, int nr, double* d_out, void* stream);
 
+/* Checkpoint and resume (no counterpart in the paper; an exact restart of a
+ * long run).  The state is a host blob: a 64-byte header (magic "LBMAXIS1",
+ * format version 1, precision, nz, nr, rho_ref, buffer parity) followed by
+ * the 9 population planes, nr x nz each with z fastest, in the solve's
+ * storage precision (FP32: deviations f_i - w_i rho_ref) and in the slot
+ * order the next step reads.  Loading it into a solve of the same precision,
+ * grid and rho_ref and stepping on gives bitwise the run that was saved.
+ * The caller owns the buffer.  lbm_axi_state_bytes: the blob size.
+ * lbm_axi_save: LBM_ERR_STATE before init, LBM_ERR_INVALID_ARG if bytes is
+ * too small; synchronous.  lbm_axi_load: LBM_ERR_INVALID_ARG for a blob that
+ * is truncated or does not match the solve (magic, version, precision, grid,
+ * rho_ref); synchronous; clears the error word.  Do not load into a solve
+ * while it belongs to a live batch (the batch keeps its own step parity). */
+int lbm_axi_state_bytes(const lbm_axi* h, size_t* bytes);
+int lbm_axi_save(lbm_axi* h, void* buf, size_t bytes);
+int lbm_axi_load(lbm_axi* h, const void* buf, size_t bytes);
+
 /* Release the solve.  NULL is a no-op.  Waits for the handle's stream. */
 void lbm_axi_destroy(lbm_axi* h);
 

@@ -544,6 +544,82 @@ int lbm_axi_moments(lbm_axi* h, double* rho, double* uz, double* ur, double* p) 
     return lbm_axi_moments_device(h, rho, uz, ur, p);
 }
 
+// ------------------------------------------------------- checkpoint --
+// Blob: StateHeader, then the 9 population planes (nr x nz each, z fastest) in
+// the storage precision, exactly as the next step will read them.
+namespace {
+struct StateHeader {
+    char magic[8];  // "LBMAXIS1"
+    int32_t version, precision, nz, nr;
+    double rho_ref;
+    int32_t cur, reserved[7];
+};
+static_assert(sizeof(StateHeader) == 64, "checkpoint header layout");
+const char kStateMagic[8] = {'L', 'B', 'M', 'A', 'X', 'I', 'S', '1'};
+
+size_t state_bytes(const lbm_axi* h) {
+    return sizeof(StateHeader) + (size_t)9 * h->nz * h->nr * (h->precision == 32 ? 4 : 8);
+}
+}  // namespace
+
+int lbm_axi_state_bytes(const lbm_axi* h, size_t* bytes) {
+    if (!h || !bytes) return LBM_ERR_INVALID_ARG;
+    *bytes = state_bytes(h);
+    return LBM_OK;
+}
+
+int lbm_axi_save(lbm_axi* h, void* buf, size_t bytes) {
+    if (!h || !buf || bytes < state_bytes(h)) return LBM_ERR_INVALID_ARG;
+    if (!h->initialized) return LBM_ERR_STATE;
+    DeviceGuard g(h->device);
+    StateHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, kStateMagic, sizeof(kStateMagic));
+    hd.version = 1;
+    hd.precision = h->precision;
+    hd.nz = h->nz;
+    hd.nr = h->nr;
+    hd.rho_ref = stored_rho_ref(h);
+    hd.cur = h->cur;
+    memcpy(buf, &hd, sizeof(hd));
+    const size_t es = h->precision == 32 ? 4 : 8;
+    char* dst = static_cast<char*>(buf) + sizeof(hd);
+    const char* src = static_cast<const char*>(h->f[h->cur]);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 9 && e == cudaSuccess; i++)
+        e = cudaMemcpy2DAsync(dst + (size_t)i * h->nz * h->nr * es, h->nz * es, src + (size_t)i * h->plane * es,
+                              (size_t)h->pitch * es, h->nz * es, h->nr, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    return read_error(h);
+}
+
+int lbm_axi_load(lbm_axi* h, const void* buf, size_t bytes) {
+    if (!h || !buf || bytes < sizeof(StateHeader)) return LBM_ERR_INVALID_ARG;
+    StateHeader hd;
+    memcpy(&hd, buf, sizeof(hd));
+    if (memcmp(hd.magic, kStateMagic, sizeof(kStateMagic)) != 0 || hd.version != 1 ||
+        hd.precision != h->precision || hd.nz != h->nz || hd.nr != h->nr || hd.rho_ref != stored_rho_ref(h) ||
+        (hd.cur != 0 && hd.cur != 1) || bytes < state_bytes(h))
+        return LBM_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    const size_t es = h->precision == 32 ? 4 : 8;
+    const char* src = static_cast<const char*>(buf) + sizeof(hd);
+    char* dst = static_cast<char*>(h->f[hd.cur]);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 9 && e == cudaSuccess; i++)
+        e = cudaMemcpy2DAsync(dst + (size_t)i * h->plane * es, (size_t)h->pitch * es,
+                              src + (size_t)i * h->nz * h->nr * es, h->nz * es, h->nz * es, h->nr,
+                              cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    h->cur = hd.cur;
+    h->initialized = true;
+    h->pending = LBM_OK;
+    return LBM_OK;
+}
+
 int lbm_axi_mass(lbm_axi* h, double* mass_rw, double* mass_plain) {
     if (!h || !mass_rw) return LBM_ERR_INVALID_ARG;
     if (!h->initialized) return LBM_ERR_STATE;

@@ -69,6 +69,9 @@ _SIGS = {
     "lbm_axi_moments": (C.c_int, [_H, _D, _D, _D, _D]),
     "lbm_axi_moments_device": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "lbm_axi_mass": (C.c_int, [_H, _D, _D]),
+    "lbm_axi_state_bytes": (C.c_int, [_H, C.POINTER(C.c_size_t)]),
+    "lbm_axi_save": (C.c_int, [_H, C.c_void_p, C.c_size_t]),
+    "lbm_axi_load": (C.c_int, [_H, C.c_void_p, C.c_size_t]),
     "lbm_axi_pressure_jump": (C.c_int, [_H, C.c_double, C.c_double, C.c_double, C.c_double, _D]),
     "lbm_axi_destroy": (None, [_H]),
     "lbm_axi_temperature": (C.c_int, [_H, _D, _D]),
@@ -233,6 +236,25 @@ def lbm_axi_mass(h):
     mr, m = C.c_double(), C.c_double()
     _check(lib().lbm_axi_mass(h, C.byref(mr), C.byref(m)), "lbm_axi_mass")
     return mr.value, m.value
+
+
+def lbm_axi_state_bytes(h):
+    n = C.c_size_t()
+    _check(lib().lbm_axi_state_bytes(h, C.byref(n)), "lbm_axi_state_bytes")
+    return n.value
+
+
+def lbm_axi_save(h):
+    """The solve's state as a bytes object (header + populations)."""
+    n = lbm_axi_state_bytes(h)
+    buf = C.create_string_buffer(n)
+    _check(lib().lbm_axi_save(h, buf, n), "lbm_axi_save")
+    return buf.raw
+
+
+def lbm_axi_load(h, blob):
+    blob = bytes(blob)
+    _check(lib().lbm_axi_load(h, blob, len(blob)), "lbm_axi_load")
 
 
 def lbm_axi_pressure_jump(h, z_c, r_c, r_in, r_out):
@@ -457,6 +479,13 @@ class Solver:
 
     def mass(self):
         return lbm_axi_mass(self.h)
+
+    def save(self):
+        return lbm_axi_save(self.h)
+
+    def load(self, blob):
+        lbm_axi_load(self.h, blob)
+        return self
 
     def pressure_jump(self, z_c, r_c, r_in, r_out):
         return lbm_axi_pressure_jump(self.h, z_c, r_c, r_in, r_out)

@@ -283,3 +283,41 @@ def test_init_physical_reports_unphysical_density():
     assert e.value.code == lbm.ERR_UNPHYSICAL
     s.init(np.full((8, 16), 0.2), physical=True).step(3)
     s.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_checkpoint_resume_is_exact(precision):
+    """Save after an odd number of steps (the other population buffer is
+    current), load into a fresh solve, step on: bitwise the uninterrupted run."""
+    from paper_1512_01977_gb300 import lbm
+
+    c = Case(45, 27)
+    rv, _ = c.coexistence()
+    rr = rv if precision == 32 else 0.0
+    fields = _droplet_fields(c, 10, du=2e-3, seed=21)
+    a = c.solver(precision, rr).init(*fields)
+    a.step(37)
+    blob = a.save()
+    assert len(blob) == lbm.lbm_axi_state_bytes(a.h)
+    a.step(40)
+    ref = a.moments()
+    b = c.solver(precision, rr).load(blob)
+    b.step(40)
+    m = b.moments()
+    for k in ("rho", "uz", "ur", "p"):
+        np.testing.assert_array_equal(m[k], ref[k])
+    assert b.mass() == a.mass()
+    # a blob of another grid, precision or rho_ref is refused; a fresh solve cannot be saved
+    for other in (Case(45, 28).solver(precision, rr), c.solver(96 - precision, rv if precision == 64 else 0.0),
+                  c.solver(precision, rr + 0.25)):
+        with pytest.raises(lbm.LbmError) as e:
+            other.load(blob)
+        assert e.value.code == lbm.ERR_INVALID_ARG
+        with pytest.raises(lbm.LbmError) as e:
+            other.save()
+        assert e.value.code == lbm.ERR_STATE
+        other.close()
+    with pytest.raises(lbm.LbmError):
+        b.load(blob[:100])
+    a.close()
+    b.close()
