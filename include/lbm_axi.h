@@ -74,6 +74,19 @@ enum {
     LBM_KAPPA_MIXED = 2    /* c_s^2 c_k^2 */
 };
 
+/* Where the axisymmetric source h_i, printed at the link midpoint (x + c_i/2,
+ * t + 1/2) in Eq. (lbm), is evaluated:
+ *   LBM_H_LOCAL     at the node, h_i(x, t) (default; every path);
+ *   LBM_H_LINK_AVG  the mean of the link's two end nodes at time t: h_i(x)/2 at
+ *                   the collision and h_i(y)/2 at the arrival node y, for the
+ *                   direction the population arrives with.  Two-kernel path only
+ *                   (the solve is created on it, the fused path is refused and
+ *                   such a solve cannot join a batch); keeps two extra sets of
+ *                   three planes.  Its radial acoustic modes decay at about
+ *                   0.7 nu k^2 instead of nu k^2: the half-link shift has no
+ *                   matching half-step in time. */
+enum { LBM_H_LOCAL = 0, LBM_H_LINK_AVG = 1 };
+
 typedef struct {
     int precision;  /* 64: FP64 populations and arithmetic; 32: FP32 populations stored as
                        deviations f_i - w_i rho_ref, FP32 arithmetic, FP64 reductions */
@@ -86,12 +99,14 @@ typedef struct {
     double rho_ref; /* reference density of the FP32 deviation storage (0 allowed) */
     double g_z;     /* constant body acceleration along z (0 in the paper's runs) */
     void* stream;   /* cudaStream_t to run on; NULL: the handle creates its own */
+    int h_eval;     /* LBM_H_*: where h_i of Eq. (lbm) is evaluated (see below) */
 } lbm_axi_opts;
 
 typedef struct lbm_axi lbm_axi;
 
 /* Fill *opts with the defaults: FP64, free-slip top, axis terms and
- * multiphase on, LBM_KAPPA_THERMO, hr_sign -1, rho_ref 0, g_z 0, own stream. */
+ * multiphase on, LBM_KAPPA_THERMO, hr_sign -1, rho_ref 0, g_z 0, own stream,
+ * LBM_H_LOCAL. */
 void lbm_axi_default_opts(lbm_axi_opts* opts);
 
 /* Create a solve on the current CUDA device.

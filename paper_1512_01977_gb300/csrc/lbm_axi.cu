@@ -63,6 +63,9 @@ Params<R> make_params(const lbm_axi* h) {
     p.multiphase = h->opts.multiphase;
     p.kappa = h->opts.kappa_mode;
     p.hr_sign = h->opts.hr_sign;
+    p.h_link = h->opts.h_eval == LBM_H_LINK_AVG && h->opts.axis_terms ? 1 : 0;
+    p.hsrc = nullptr;
+    p.hdst = nullptr;
     return p;
 }
 
@@ -109,14 +112,16 @@ cudaError_t enqueue_step(lbm_axi* h) {
         return e;
     }
     if (h->precision == 32) {
-        e = Ops<float>::density(h->pf, (const float*)h->f[c], (float*)h->aux, h->derr, h->stream);
+        const Params<float> p = link_params(h, h->pf, c);
+        e = Ops<float>::density(p, (const float*)h->f[c], (float*)h->aux, h->derr, h->stream);
         if (e == cudaSuccess)
-            e = Ops<float>::update(h->pf, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1], (const float*)h->aux,
+            e = Ops<float>::update(p, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1], (const float*)h->aux,
                                    h->stream);
     } else {
-        e = Ops<double>::density(h->pdd, (const double*)h->f[c], (double*)h->aux, h->derr, h->stream);
+        const Params<double> p = link_params(h, h->pdd, c);
+        e = Ops<double>::density(p, (const double*)h->f[c], (double*)h->aux, h->derr, h->stream);
         if (e == cudaSuccess)
-            e = Ops<double>::update(h->pdd, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
+            e = Ops<double>::update(p, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
                                     (const double*)h->aux, h->stream);
     }
     h->cur = c ^ 1;
@@ -125,8 +130,10 @@ cudaError_t enqueue_step(lbm_axi* h) {
 
 cudaError_t enqueue_density(lbm_axi* h) {
     if (h->precision == 32)
-        return Ops<float>::density(h->pf, (const float*)h->f[h->cur], (float*)h->aux, h->derr, h->stream);
-    return Ops<double>::density(h->pdd, (const double*)h->f[h->cur], (double*)h->aux, h->derr, h->stream);
+        return Ops<float>::density(link_params(h, h->pf, h->cur), (const float*)h->f[h->cur], (float*)h->aux,
+                                   h->derr, h->stream);
+    return Ops<double>::density(link_params(h, h->pdd, h->cur), (const double*)h->f[h->cur], (double*)h->aux,
+                                h->derr, h->stream);
 }
 
 // Graph of an even number of steps starting and ending in buffer 0.
@@ -210,6 +217,8 @@ void release_all(lbm_axi* h) {
     dev_free(h->derr, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->d_self, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->d_self_start, h->via_hook, h->hook_ctx, h->hook_release);
+    dev_free(h->hb[0], h->via_hook, h->hook_ctx, h->hook_release);
+    dev_free(h->hb[1], h->via_hook, h->hook_ctx, h->hook_release);
     if (h->herr) cudaFreeHost(h->herr);
     if (h->hred) cudaFreeHost(h->hred);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -231,6 +240,7 @@ void lbm_axi_default_opts(lbm_axi_opts* o) {
     o->rho_ref = 0.0;
     o->g_z = 0.0;
     o->stream = nullptr;
+    o->h_eval = LBM_H_LOCAL;
 }
 
 size_t lbm_axi_footprint(int nz, int nr, int precision) {
@@ -252,6 +262,7 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     if (o.precision != 32 && o.precision != 64) return LBM_ERR_INVALID_ARG;
     if (o.top_bc < 0 || o.top_bc > 2 || o.kappa_mode < 0 || o.kappa_mode > 2) return LBM_ERR_INVALID_ARG;
     if (o.hr_sign != 1 && o.hr_sign != -1) return LBM_ERR_INVALID_ARG;
+    if (o.h_eval != LBM_H_LOCAL && o.h_eval != LBM_H_LINK_AVG) return LBM_ERR_INVALID_ARG;
     lbm_eos e;
     memset(&e, 0, sizeof(e));
     double T = 0.0, Tc = 0.0;
@@ -300,8 +311,14 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     h->d_self = dev_alloc(o.precision == 32 ? sizeof(lbm::BatchSolve<float>) : sizeof(lbm::BatchSolve<double>));
     h->d_self_start = (long long*)dev_alloc(2 * sizeof(long long));
     h->bytes = lbm_axi_footprint(nz, nr, o.precision);
+    const bool link = o.h_eval == LBM_H_LINK_AVG && o.axis_terms;
+    if (link) {
+        h->hb[0] = dev_alloc(3 * plane_bytes);
+        h->hb[1] = dev_alloc(3 * plane_bytes);
+        h->bytes += 6 * plane_bytes;
+    }
     bool ok = h->f[0] && h->f[1] && h->aux && h->mout && h->partial && h->dred && h->derr && h->d_self &&
-              h->d_self_start;
+              h->d_self_start && (!link || (h->hb[0] && h->hb[1]));
     ok = ok && cudaMallocHost(&h->herr, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost(&h->hred, 4 * sizeof(double)) == cudaSuccess;
     if (!ok) {
@@ -323,7 +340,8 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     }
     h->pf = make_params<float>(h);
     h->pdd = make_params<double>(h);
-    h->path = nr >= lbm::kStepMinRows ? LBM_PATH_FUSED : LBM_PATH_SPLIT;
+    // the link-midpoint source is implemented on the two-kernel path only
+    h->path = nr >= lbm::kStepMinRows && !link ? LBM_PATH_FUSED : LBM_PATH_SPLIT;
     h->rows_per_cta = 0;  // balanced single wave
     if (h->precision == 32) h->pdd = make_params_out(h);
     *h->herr = 0;
@@ -362,6 +380,9 @@ int lbm_axi_init_device(lbm_axi* h, const double* rho, const double* uz, const d
         e = Ops<double>::init(h->pdd, stored_rho_ref(h), rho, uz, ur, (double*)h->f[0], h->stream);
     }
     h->cur = 0;
+    // no arrival halves are pending at the start
+    for (int q = 0; q < 2 && e == cudaSuccess && h->hb[0]; q++)
+        e = cudaMemsetAsync(h->hb[q], 0, 3 * (size_t)h->plane * (h->precision == 32 ? 4 : 8), h->stream);
     if (e != cudaSuccess) return LBM_ERR_CUDA;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ERR_CUDA;
     h->initialized = true;
@@ -495,11 +516,11 @@ int lbm_axi_time_kernels(lbm_axi* h, long long n, double* ms) {
             h->cur = c;
         } else if (e == cudaSuccess) {
             if (h->precision == 32)
-                e = Ops<float>::update(h->pf, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1],
-                                       (const float*)h->aux, h->stream);
+                e = Ops<float>::update(link_params(h, h->pf, c), h->pdd, (const float*)h->f[c],
+                                       (float*)h->f[c ^ 1], (const float*)h->aux, h->stream);
             else
-                e = Ops<double>::update(h->pdd, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
-                                        (const double*)h->aux, h->stream);
+                e = Ops<double>::update(link_params(h, h->pdd, c), h->pdd, (const double*)h->f[c],
+                                        (double*)h->f[c ^ 1], (const double*)h->aux, h->stream);
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
@@ -557,8 +578,10 @@ struct StateHeader {
 static_assert(sizeof(StateHeader) == 64, "checkpoint header layout");
 const char kStateMagic[8] = {'L', 'B', 'M', 'A', 'X', 'I', 'S', '1'};
 
+// planes in the blob: the 9 populations, then (link-midpoint source) the 3 source planes
+int state_planes(const lbm_axi* h) { return h->hb[0] ? 12 : 9; }
 size_t state_bytes(const lbm_axi* h) {
-    return sizeof(StateHeader) + (size_t)9 * h->nz * h->nr * (h->precision == 32 ? 4 : 8);
+    return sizeof(StateHeader) + (size_t)state_planes(h) * h->nz * h->nr * (h->precision == 32 ? 4 : 8);
 }
 }  // namespace
 
@@ -581,14 +604,18 @@ int lbm_axi_save(lbm_axi* h, void* buf, size_t bytes) {
     hd.nr = h->nr;
     hd.rho_ref = stored_rho_ref(h);
     hd.cur = h->cur;
+    hd.reserved[0] = h->hb[0] ? 1 : 0;
     memcpy(buf, &hd, sizeof(hd));
     const size_t es = h->precision == 32 ? 4 : 8;
     char* dst = static_cast<char*>(buf) + sizeof(hd);
     const char* src = static_cast<const char*>(h->f[h->cur]);
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 9 && e == cudaSuccess; i++)
-        e = cudaMemcpy2DAsync(dst + (size_t)i * h->nz * h->nr * es, h->nz * es, src + (size_t)i * h->plane * es,
-                              (size_t)h->pitch * es, h->nz * es, h->nr, cudaMemcpyDeviceToHost, h->stream);
+    for (int i = 0; i < state_planes(h) && e == cudaSuccess; i++) {
+        const char* s = i < 9 ? src + (size_t)i * h->plane * es
+                              : static_cast<const char*>(h->hb[h->cur]) + (size_t)(i - 9) * h->plane * es;
+        e = cudaMemcpy2DAsync(dst + (size_t)i * h->nz * h->nr * es, h->nz * es, s, (size_t)h->pitch * es,
+                              h->nz * es, h->nr, cudaMemcpyDeviceToHost, h->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return LBM_ERR_CUDA;
     return read_error(h);
@@ -600,17 +627,19 @@ int lbm_axi_load(lbm_axi* h, const void* buf, size_t bytes) {
     memcpy(&hd, buf, sizeof(hd));
     if (memcmp(hd.magic, kStateMagic, sizeof(kStateMagic)) != 0 || hd.version != 1 ||
         hd.precision != h->precision || hd.nz != h->nz || hd.nr != h->nr || hd.rho_ref != stored_rho_ref(h) ||
-        (hd.cur != 0 && hd.cur != 1) || bytes < state_bytes(h))
+        (hd.cur != 0 && hd.cur != 1) || hd.reserved[0] != (h->hb[0] ? 1 : 0) || bytes < state_bytes(h))
         return LBM_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     const size_t es = h->precision == 32 ? 4 : 8;
     const char* src = static_cast<const char*>(buf) + sizeof(hd);
     char* dst = static_cast<char*>(h->f[hd.cur]);
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < 9 && e == cudaSuccess; i++)
-        e = cudaMemcpy2DAsync(dst + (size_t)i * h->plane * es, (size_t)h->pitch * es,
-                              src + (size_t)i * h->nz * h->nr * es, h->nz * es, h->nz * es, h->nr,
-                              cudaMemcpyHostToDevice, h->stream);
+    for (int i = 0; i < state_planes(h) && e == cudaSuccess; i++) {
+        char* d = i < 9 ? dst + (size_t)i * h->plane * es
+                        : static_cast<char*>(h->hb[hd.cur]) + (size_t)(i - 9) * h->plane * es;
+        e = cudaMemcpy2DAsync(d, (size_t)h->pitch * es, src + (size_t)i * h->nz * h->nr * es, h->nz * es,
+                              h->nz * es, h->nr, cudaMemcpyHostToDevice, h->stream);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return LBM_ERR_CUDA;
@@ -680,7 +709,7 @@ int lbm_axi_get_tuning(const lbm_axi* h, lbm_axi_tuning* t) {
 int lbm_axi_set_tuning(lbm_axi* h, const lbm_axi_tuning* t) {
     if (!h || !t) return LBM_ERR_INVALID_ARG;
     if (t->path != LBM_PATH_FUSED && t->path != LBM_PATH_SPLIT) return LBM_ERR_INVALID_ARG;
-    if (t->path == LBM_PATH_FUSED && h->nr < lbm::kStepMinRows) return LBM_ERR_INVALID_ARG;
+    if (t->path == LBM_PATH_FUSED && (h->nr < lbm::kStepMinRows || h->hb[0])) return LBM_ERR_INVALID_ARG;
     if (t->rows_per_cta < 0 || t->rows_per_cta > (1 << 20)) return LBM_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ERR_CUDA;

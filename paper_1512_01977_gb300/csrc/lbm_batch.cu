@@ -163,7 +163,7 @@ int lbm_axi_batch_create(lbm_axi* const* solves, int n, void* stream, lbm_axi_ba
         const lbm_axi* h = solves[i];
         if (!h || !h->initialized || h->device != dev || h->precision != h0->precision ||
             h->nr < lbm::kStepMinRows || h->opts.multiphase != h0->opts.multiphase ||
-            h->opts.axis_terms != h0->opts.axis_terms)
+            h->opts.axis_terms != h0->opts.axis_terms || h->hb[0])  // (no link-midpoint source in the batch)
             return LBM_ERR_INVALID_ARG;
         for (int k = 0; k < i; k++)
             if (solves[k] == h) return LBM_ERR_INVALID_ARG;
@@ -373,19 +373,21 @@ int lbm_axi_autotune(lbm_axi* h, int trials, lbm_axi_tuning* chosen) {
     auto split = [&]() {
         cudaError_t e;
         if (h->precision == 32) {
-            e = Ops<float>::density(h->pf, (const float*)h->f[c], (float*)h->aux, h->derr, h->stream);
+            const Params<float> p = link_params(h, h->pf, c);
+            e = Ops<float>::density(p, (const float*)h->f[c], (float*)h->aux, h->derr, h->stream);
             if (e == cudaSuccess)
-                e = Ops<float>::update(h->pf, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1],
+                e = Ops<float>::update(p, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1],
                                        (const float*)h->aux, h->stream);
         } else {
-            e = Ops<double>::density(h->pdd, (const double*)h->f[c], (double*)h->aux, h->derr, h->stream);
+            const Params<double> p = link_params(h, h->pdd, c);
+            e = Ops<double>::density(p, (const double*)h->f[c], (double*)h->aux, h->derr, h->stream);
             if (e == cudaSuccess)
-                e = Ops<double>::update(h->pdd, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
+                e = Ops<double>::update(p, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
                                         (const double*)h->aux, h->stream);
         }
         return e;
     };
-    if (h->nr >= lbm::kStepMinRows) {
+    if (h->nr >= lbm::kStepMinRows && !h->hb[0]) {  // the fused forms lack the link-midpoint source
         const int rows_list[5] = {0, 32, 64, 144, 256};
         for (int q = 0; q < 5; q++) {
             const float ms = time_launches(h->stream, trials, [&] { return fused(rows_list[q]); });

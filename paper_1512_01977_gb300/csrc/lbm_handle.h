@@ -42,7 +42,19 @@ struct lbm_axi {
     long long* d_self_start;  // {0, strips * nr}
     Params<float> pf;
     Params<double> pdd;
+    void* hb[2];  // h at the link midpoint: S0, H_z, H_r planes of the step that wrote f[c] (else null)
 };
+
+// Parameters of a step that reads f[c] (and writes f[c^1]), with the source
+// planes of the link-midpoint reading attached when the solve uses it.
+template <typename R>
+inline Params<R> link_params(const lbm_axi* h, Params<R> p, int c) {
+    if (h->hb[0]) {
+        p.hsrc = static_cast<const R*>(h->hb[c]);
+        p.hdst = static_cast<R*>(h->hb[c ^ 1]);
+    }
+    return p;
+}
 
 // Step parity bookkeeping used by the batch API: after n steps run outside
 // the handle's own step loop, its current buffer flips when n is odd.

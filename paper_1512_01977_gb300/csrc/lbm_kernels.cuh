@@ -34,6 +34,13 @@ __global__ void __launch_bounds__(256) k_density(Params<R> p, const R* __restric
         jz += R(cz_of(i)) * fi;
         jr += R(cr_of(i)) * fi;
     }
+    if (p.h_link) {
+        // arrival halves h_i(y)/2: zeroth moment S0/2, first moment H/2
+        const long long o = (long long)j * p.pitch + k;
+        drho += R(0.5) * p.hsrc[o];
+        jz += R(0.5) * p.hsrc[p.plane + o];
+        jr += R(0.5) * p.hsrc[2 * p.plane + o];
+    }
     const R rho = p.rho_ref + drho;
     R psi = R(0);
     int bad = 0;
@@ -252,11 +259,24 @@ __global__ void __launch_bounds__(256) k_update(Params<R> p, Params<double> pd, 
         const R sz = R(2) * u0z + duz, sr = R(2) * u0r + dur;  // u0 + u1
         const R dusum = duz * sz + dur * sr;                   // u1^2 - u0^2
         const long long o = (long long)j * p.pitch + k;
+        // link-midpoint source: arrival half of the previous step's h at this
+        // node, departure half of this step's; this step's S0, H kept for the next
+        R a0 = R(0), az = R(0), ar = R(0), hs = R(1);
+        if (p.h_link) {
+            a0 = p.hsrc[o];
+            az = p.hsrc[p.plane + o];
+            ar = p.hsrc[2 * p.plane + o];
+            p.hdst[o] = m0;
+            p.hdst[p.plane + o] = Hz;
+            p.hdst[2 * p.plane + o] = Hr;
+            hs = R(0.5);
+        }
 #pragma unroll
         for (int i = 0; i < Q; i++) {
             const R w = w_of<R>(i);
             const R cx = R(cz_of(i)), cy = R(cr_of(i));
-            const R fi = f[pull_slot(p, k, j, i)];
+            R fi = f[pull_slot(p, k, j, i)];
+            if (p.h_link) fi += R(0.5) * w * (a0 + R(3) * (cx * az + cy * ar));
             const R cu0 = cx * u0z + cy * u0r;
             const R cdu = cx * duz + cy * dur;
             const R csum = cx * sz + cy * sr;
@@ -264,7 +284,7 @@ __global__ void __launch_bounds__(256) k_update(Params<R> p, Params<double> pd, 
             // f^eq(rho, u0 + F/rho) - f^eq(rho, u0) written as a difference, and h_i (Sec. II.B).
             const R feq = w * (drho + rho * (R(3) * cu0 + R(4.5) * cu0 * cu0 - R(1.5) * u0sq));
             const R edm = w * rho * (R(3) * cdu + R(4.5) * cdu * csum - R(1.5) * dusum);
-            const R h = w * (m0 + R(3) * (cx * Hz + cy * Hr));
+            const R h = hs * w * (m0 + R(3) * (cx * Hz + cy * Hr));
             fout[i * p.plane + o] = fi + (feq - fi) * p.tau_inv + edm + h;
         }
     }

@@ -24,11 +24,12 @@ class Case:
     hr_sign: int = -1
     gz: float = 0.0
     r0: float = 0.0  # oracle only: radial offset of a window cut from a larger lattice
+    h_eval: int = O.H_LOCAL
 
     def oracle_params(self):
         p = O.Params(nz=self.nz, nr=self.nr, tau=self.tau, A=self.A, eos=self.eos, lam=self.lam, top=self.top,
                      axis=self.axis, multiphase=self.multiphase, kappa=self.kappa, hr_sign=self.hr_sign,
-                     gz=self.gz, r0=self.r0)
+                     gz=self.gz, r0=self.r0, h_eval=self.h_eval)
         Tc, _ = O.eos.critical_point(p)
         return p.replace(T=self.T_over_Tc * Tc)
 
@@ -41,7 +42,7 @@ class Case:
         eos = lbm.make_eos(self.eos, self.T_over_Tc, lam=self.lam) if self.multiphase else None
         return lbm.Solver(self.nz, self.nr, self.tau, eos=eos, A=self.A, precision=precision, top=self.top,
                           axis=self.axis, multiphase=self.multiphase, kappa=self.kappa, hr_sign=self.hr_sign,
-                          rho_ref=rho_ref, g_z=self.gz)
+                          rho_ref=rho_ref, g_z=self.gz, h_eval=self.h_eval)
 
 
 def run_oracle(case, fields, steps):

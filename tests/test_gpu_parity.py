@@ -321,3 +321,51 @@ def test_checkpoint_resume_is_exact(precision):
         b.load(blob[:100])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("top", [O.TOP_FREESLIP, O.TOP_NOSLIP])
+def test_link_midpoint_source_fp64(top):
+    """h_eval = LINK_AVG (two-kernel path) against the oracle's link average:
+    a droplet from rest with a random flow, and the radial acoustic mode."""
+    from scipy import special
+
+    c = Case(45, 27, top=top, h_eval=O.H_LINK_AVG)
+    fields = _droplet_fields(c, 10, du=2e-3, seed=31)
+    o = O.Oracle(c.oracle_params()).init(*fields, physical=True).step(90)
+    s = c.solver().init(*fields, physical=True)
+    from paper_1512_01977_gb300 import lbm
+
+    assert lbm.lbm_axi_get_tuning(s.h)[0] == lbm.PATH_SPLIT
+    s.step(90)
+    mo, mg = o.moments(), s.moments()
+    assert rel_err(mg["rho"], mo["rho"]) <= TOL64 and vel_err(mg, mo) <= TOL64 and rel_err(mg["p"], mo["p"]) <= TOL64
+    assert mg["rho"].size and s.mass()[0] == pytest.approx(o.mass_rweighted(), rel=1e-12)
+    s.close()
+    c = Case(3, 32, multiphase=0, tau=0.8, top=top, h_eval=O.H_LINK_AVG)
+    _compare(c, I.radial_mode(3, 32, 1.0, 1e-2, special.jn_zeros(1, 1)[0] / 32), 40)
+
+
+def test_link_midpoint_source_limits():
+    """A LINK_AVG solve refuses the fused path and batches; its checkpoint
+    carries the source planes (bitwise resume)."""
+    from paper_1512_01977_gb300 import lbm
+
+    c = Case(40, 24, h_eval=O.H_LINK_AVG)
+    fields = _droplet_fields(c, 9, du=1e-3, seed=32)
+    s = c.solver(32, c.coexistence()[0]).init(*fields, physical=True)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_axi_set_tuning(s.h, lbm.PATH_FUSED, 0)
+    with pytest.raises(lbm.LbmError):
+        lbm.Batch([s])
+    s.step(11)
+    blob = s.save()
+    s.step(20)
+    ref = s.moments()
+    t = c.solver(32, c.coexistence()[0]).load(blob).step(20)
+    np.testing.assert_array_equal(t.moments()["rho"], ref["rho"])
+    # a LOCAL solve of the same grid refuses the blob
+    u = Case(40, 24).solver(32, c.coexistence()[0])
+    with pytest.raises(lbm.LbmError):
+        u.load(blob)
+    for x in (s, t, u):
+        x.close()
