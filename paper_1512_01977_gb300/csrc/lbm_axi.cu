@@ -63,9 +63,6 @@ Params<R> make_params(const lbm_axi* h) {
     p.multiphase = h->opts.multiphase;
     p.kappa = h->opts.kappa_mode;
     p.hr_sign = h->opts.hr_sign;
-    p.h_link = h->opts.h_eval == LBM_H_LINK_AVG && h->opts.axis_terms ? 1 : 0;
-    p.hsrc = nullptr;
-    p.hdst = nullptr;
     return p;
 }
 
@@ -112,17 +109,17 @@ cudaError_t enqueue_step(lbm_axi* h) {
         return e;
     }
     if (h->precision == 32) {
-        const Params<float> p = link_params(h, h->pf, c);
-        e = Ops<float>::density(p, (const float*)h->f[c], (float*)h->aux, h->derr, h->stream);
+        const lbm::LinkPlanes<float> lk = link_planes<float>(h, c);
+        e = Ops<float>::density(h->pf, (const float*)h->f[c], (float*)h->aux, h->derr, h->stream, lk);
         if (e == cudaSuccess)
-            e = Ops<float>::update(p, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1], (const float*)h->aux,
-                                   h->stream);
+            e = Ops<float>::update(h->pf, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1], (const float*)h->aux,
+                                   h->stream, lk);
     } else {
-        const Params<double> p = link_params(h, h->pdd, c);
-        e = Ops<double>::density(p, (const double*)h->f[c], (double*)h->aux, h->derr, h->stream);
+        const lbm::LinkPlanes<double> lk = link_planes<double>(h, c);
+        e = Ops<double>::density(h->pdd, (const double*)h->f[c], (double*)h->aux, h->derr, h->stream, lk);
         if (e == cudaSuccess)
-            e = Ops<double>::update(p, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
-                                    (const double*)h->aux, h->stream);
+            e = Ops<double>::update(h->pdd, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
+                                    (const double*)h->aux, h->stream, lk);
     }
     h->cur = c ^ 1;
     return e;
@@ -130,10 +127,10 @@ cudaError_t enqueue_step(lbm_axi* h) {
 
 cudaError_t enqueue_density(lbm_axi* h) {
     if (h->precision == 32)
-        return Ops<float>::density(link_params(h, h->pf, h->cur), (const float*)h->f[h->cur], (float*)h->aux,
-                                   h->derr, h->stream);
-    return Ops<double>::density(link_params(h, h->pdd, h->cur), (const double*)h->f[h->cur], (double*)h->aux,
-                                h->derr, h->stream);
+        return Ops<float>::density(h->pf, (const float*)h->f[h->cur], (float*)h->aux, h->derr, h->stream,
+                                   link_planes<float>(h, h->cur));
+    return Ops<double>::density(h->pdd, (const double*)h->f[h->cur], (double*)h->aux, h->derr, h->stream,
+                                link_planes<double>(h, h->cur));
 }
 
 // Graph of an even number of steps starting and ending in buffer 0.
@@ -516,11 +513,11 @@ int lbm_axi_time_kernels(lbm_axi* h, long long n, double* ms) {
             h->cur = c;
         } else if (e == cudaSuccess) {
             if (h->precision == 32)
-                e = Ops<float>::update(link_params(h, h->pf, c), h->pdd, (const float*)h->f[c],
-                                       (float*)h->f[c ^ 1], (const float*)h->aux, h->stream);
+                e = Ops<float>::update(h->pf, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1],
+                                       (const float*)h->aux, h->stream, link_planes<float>(h, c));
             else
-                e = Ops<double>::update(link_params(h, h->pdd, c), h->pdd, (const double*)h->f[c],
-                                        (double*)h->f[c ^ 1], (const double*)h->aux, h->stream);
+                e = Ops<double>::update(h->pdd, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
+                                        (const double*)h->aux, h->stream, link_planes<double>(h, c));
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);

@@ -373,17 +373,17 @@ int lbm_axi_autotune(lbm_axi* h, int trials, lbm_axi_tuning* chosen) {
     auto split = [&]() {
         cudaError_t e;
         if (h->precision == 32) {
-            const Params<float> p = link_params(h, h->pf, c);
-            e = Ops<float>::density(p, (const float*)h->f[c], (float*)h->aux, h->derr, h->stream);
+            const lbm::LinkPlanes<float> lk = link_planes<float>(h, c);
+            e = Ops<float>::density(h->pf, (const float*)h->f[c], (float*)h->aux, h->derr, h->stream, lk);
             if (e == cudaSuccess)
-                e = Ops<float>::update(p, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1],
-                                       (const float*)h->aux, h->stream);
+                e = Ops<float>::update(h->pf, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1],
+                                       (const float*)h->aux, h->stream, lk);
         } else {
-            const Params<double> p = link_params(h, h->pdd, c);
-            e = Ops<double>::density(p, (const double*)h->f[c], (double*)h->aux, h->derr, h->stream);
+            const lbm::LinkPlanes<double> lk = link_planes<double>(h, c);
+            e = Ops<double>::density(h->pdd, (const double*)h->f[c], (double*)h->aux, h->derr, h->stream, lk);
             if (e == cudaSuccess)
-                e = Ops<double>::update(p, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
-                                        (const double*)h->aux, h->stream);
+                e = Ops<double>::update(h->pdd, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
+                                        (const double*)h->aux, h->stream, lk);
         }
         return e;
     };

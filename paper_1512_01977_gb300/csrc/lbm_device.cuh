@@ -54,12 +54,16 @@ struct Params {
     int eos;           // EOS_*
     R T, a, b, Rg, lambda;
     int top, axis, multiphase, kappa, hr_sign;
-    // h_i at the link midpoint (two-kernel path only): the step that reads the
-    // populations adds the arrival half h_i(y)/2 from hsrc (the S0 = -rho u_r/r,
-    // H_z, H_r planes of the step that wrote them) and writes its own to hdst.
-    int h_link;
-    const R* hsrc;
-    R* hdst;
+};
+
+// h_i at the link midpoint (two-kernel path only): the step that reads the
+// populations adds the arrival half h_i(y)/2 from src (the S0 = -rho u_r/r,
+// H_z, H_r planes of the step that wrote them) and writes its own to dst.
+// Null pointers: h_i at the node.
+template <typename R>
+struct LinkPlanes {
+    const R* src;
+    R* dst;
 };
 
 // One solve of a batched launch: its parameters and its two population buffers

@@ -45,15 +45,12 @@ struct lbm_axi {
     void* hb[2];  // h at the link midpoint: S0, H_z, H_r planes of the step that wrote f[c] (else null)
 };
 
-// Parameters of a step that reads f[c] (and writes f[c^1]), with the source
-// planes of the link-midpoint reading attached when the solve uses it.
+// Source planes of the link-midpoint reading for a step that reads f[c] (and
+// writes f[c^1]); null pointers when the solve evaluates h_i at the node.
 template <typename R>
-inline Params<R> link_params(const lbm_axi* h, Params<R> p, int c) {
-    if (h->hb[0]) {
-        p.hsrc = static_cast<const R*>(h->hb[c]);
-        p.hdst = static_cast<R*>(h->hb[c ^ 1]);
-    }
-    return p;
+inline lbm::LinkPlanes<R> link_planes(const lbm_axi* h, int c) {
+    if (!h->hb[0]) return {nullptr, nullptr};
+    return {static_cast<const R*>(h->hb[c]), static_cast<R*>(h->hb[c ^ 1])};
 }
 
 // Step parity bookkeeping used by the batch API: after n steps run outside

@@ -22,7 +22,7 @@ namespace lbm {
 // rho <= 0, psi^2 < 0 and non-finite values; never traps.
 template <typename R>
 __global__ void __launch_bounds__(256) k_density(Params<R> p, const R* __restrict__ f, R* __restrict__ aux,
-                                                 int* __restrict__ err) {
+                                                 int* __restrict__ err, LinkPlanes<R> lk) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (k >= p.nz || j >= p.nr) return;
@@ -34,12 +34,12 @@ __global__ void __launch_bounds__(256) k_density(Params<R> p, const R* __restric
         jz += R(cz_of(i)) * fi;
         jr += R(cr_of(i)) * fi;
     }
-    if (p.h_link) {
+    if (lk.src) {
         // arrival halves h_i(y)/2: zeroth moment S0/2, first moment H/2
         const long long o = (long long)j * p.pitch + k;
-        drho += R(0.5) * p.hsrc[o];
-        jz += R(0.5) * p.hsrc[p.plane + o];
-        jr += R(0.5) * p.hsrc[2 * p.plane + o];
+        drho += R(0.5) * lk.src[o];
+        jz += R(0.5) * lk.src[p.plane + o];
+        jr += R(0.5) * lk.src[2 * p.plane + o];
     }
     const R rho = p.rho_ref + drho;
     R psi = R(0);
@@ -115,7 +115,7 @@ struct TileShape {
 template <typename R, int TZ, int TR, bool MOMENTS>
 __global__ void __launch_bounds__(256) k_update(Params<R> p, Params<double> pd, const R* __restrict__ f,
                                                 R* __restrict__ fout, const R* __restrict__ aux,
-                                                double* __restrict__ mout) {
+                                                double* __restrict__ mout, LinkPlanes<R> lk) {
     using S = TileShape<TZ, TR>;
     constexpr int PW = S::PW, PH = S::PH, DW = S::DW, DH = S::DH, UW = S::UW, UH = S::UH;
     constexpr int NT = 256;
@@ -262,13 +262,13 @@ __global__ void __launch_bounds__(256) k_update(Params<R> p, Params<double> pd, 
         // link-midpoint source: arrival half of the previous step's h at this
         // node, departure half of this step's; this step's S0, H kept for the next
         R a0 = R(0), az = R(0), ar = R(0), hs = R(1);
-        if (p.h_link) {
-            a0 = p.hsrc[o];
-            az = p.hsrc[p.plane + o];
-            ar = p.hsrc[2 * p.plane + o];
-            p.hdst[o] = m0;
-            p.hdst[p.plane + o] = Hz;
-            p.hdst[2 * p.plane + o] = Hr;
+        if (lk.src) {
+            a0 = lk.src[o];
+            az = lk.src[p.plane + o];
+            ar = lk.src[2 * p.plane + o];
+            lk.dst[o] = m0;
+            lk.dst[p.plane + o] = Hz;
+            lk.dst[2 * p.plane + o] = Hr;
             hs = R(0.5);
         }
 #pragma unroll
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) k_update(Params<R> p, Params<double> pd, 
             const R w = w_of<R>(i);
             const R cx = R(cz_of(i)), cy = R(cr_of(i));
             R fi = f[pull_slot(p, k, j, i)];
-            if (p.h_link) fi += R(0.5) * w * (a0 + R(3) * (cx * az + cy * ar));
+            if (lk.src) fi += R(0.5) * w * (a0 + R(3) * (cx * az + cy * ar));
             const R cu0 = cx * u0z + cy * u0r;
             const R cdu = cx * duz + cy * dur;
             const R csum = cx * sz + cy * sr;

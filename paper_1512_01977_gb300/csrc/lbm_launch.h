@@ -17,10 +17,12 @@ constexpr int kStripNarrow = 64, kStripWide = 96;
 template <typename R>
 struct Ops {
     // kernel (a): gather, rho/j, psi; raises bits in *err.
-    static cudaError_t density(const Params<R>& p, const R* f, R* aux, int* err, cudaStream_t s);
+    // lk: the link-midpoint source planes (null: h_i at the node).
+    static cudaError_t density(const Params<R>& p, const R* f, R* aux, int* err, cudaStream_t s,
+                               LinkPlanes<R> lk = {nullptr, nullptr});
     // kernel (b): the fused stream + force + EDM + axisymmetric source + collide step.
     static cudaError_t update(const Params<R>& p, const Params<double>& pd, const R* f, R* fout, const R* aux,
-                              cudaStream_t s);
+                              cudaStream_t s, LinkPlanes<R> lk = {nullptr, nullptr});
     // rho, physical u, P_k of the current state into mout[4][nz*nr] (after density()).
     static cudaError_t moments(const Params<R>& p, const Params<double>& pd, const R* f, const R* aux,
                                double* mout, cudaStream_t s);

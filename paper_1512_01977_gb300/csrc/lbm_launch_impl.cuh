@@ -27,14 +27,14 @@ size_t Ops<R>::update_smem() {
 
 template <typename R>
 static cudaError_t launch_update(const Params<R>& p, const Params<double>& pd, const R* f, R* fout, const R* aux,
-                                 double* mout, bool moments, cudaStream_t s) {
+                                 double* mout, bool moments, cudaStream_t s, LinkPlanes<R> lk) {
     using T = UpdateTile<R>;
     const size_t smem = Ops<R>::update_smem();
     dim3 grid((p.nz + T::TZ - 1) / T::TZ, (p.nr + T::TR - 1) / T::TR);
     if (moments) {
-        k_update<R, T::TZ, T::TR, true><<<grid, 256, smem, s>>>(p, pd, f, nullptr, aux, mout);
+        k_update<R, T::TZ, T::TR, true><<<grid, 256, smem, s>>>(p, pd, f, nullptr, aux, mout, lk);
     } else {
-        k_update<R, T::TZ, T::TR, false><<<grid, 256, smem, s>>>(p, pd, f, fout, aux, nullptr);
+        k_update<R, T::TZ, T::TR, false><<<grid, 256, smem, s>>>(p, pd, f, fout, aux, nullptr, lk);
     }
     return cudaGetLastError();
 }
@@ -142,22 +142,22 @@ cudaError_t Ops<R>::step(const Params<R>& p, const R* f, R* fout, int rows_per_c
 }
 
 template <typename R>
-cudaError_t Ops<R>::density(const Params<R>& p, const R* f, R* aux, int* err, cudaStream_t s) {
+cudaError_t Ops<R>::density(const Params<R>& p, const R* f, R* aux, int* err, cudaStream_t s, LinkPlanes<R> lk) {
     dim3 block(32, 8), grid((p.nz + 31) / 32, (p.nr + 7) / 8);
-    k_density<R><<<grid, block, 0, s>>>(p, f, aux, err);
+    k_density<R><<<grid, block, 0, s>>>(p, f, aux, err, lk);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t Ops<R>::update(const Params<R>& p, const Params<double>& pd, const R* f, R* fout, const R* aux,
-                           cudaStream_t s) {
-    return launch_update<R>(p, pd, f, fout, aux, nullptr, false, s);
+                           cudaStream_t s, LinkPlanes<R> lk) {
+    return launch_update<R>(p, pd, f, fout, aux, nullptr, false, s, lk);
 }
 
 template <typename R>
 cudaError_t Ops<R>::moments(const Params<R>& p, const Params<double>& pd, const R* f, const R* aux, double* mout,
                             cudaStream_t s) {
-    return launch_update<R>(p, pd, f, nullptr, aux, mout, true, s);
+    return launch_update<R>(p, pd, f, nullptr, aux, mout, true, s, LinkPlanes<R>{nullptr, nullptr});
 }
 
 template <typename R>
