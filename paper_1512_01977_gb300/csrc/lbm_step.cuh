@@ -402,7 +402,16 @@ __device__ __forceinline__ double2 pk(double a, double b) { return make_double2(
 __device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+// a - b as one packed subtract (sub.rn.f32x2), without a (-1, -1) operand pair
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+    unsigned long long x, y, d;
+    memcpy(&x, &a, 8);
+    memcpy(&y, &b, 8);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+    float2 r;
+    memcpy(&r, &d, 8);
+    return r;
+}
 __device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
 __device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {

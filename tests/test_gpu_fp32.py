@@ -43,7 +43,7 @@ def _errors(case, fields, steps, rho_ref):
             "mass": abs(mr / o.mass_rweighted() - 1)}
 
 
-def test_droplet_c1_fp32():
+def test_droplet_64x64_fp32():
     c = Case(64, 64)
     rv, rl = c.coexistence()
     e = _errors(c, I.droplet(64, 64, 16, rl, rv), 2000, rho_ref=rv)

@@ -130,12 +130,12 @@ def test_radial_wave_channel_fp64():
     _compare(c, fields, 300)
 
 
-def test_c1_droplet_full_fp64():
+def test_droplet_64x64_full_fp64():
     """64 x 64 droplet (CS, T = 0.8 Tc, A = -0.152, tau = 1, R = 16, tanh width 2),
     the full 2000 steps."""
     c = Case(64, 64)
     errs = _compare(c, _droplet_fields(c, 16), 2000)
-    print("C1 parity", errs)
+    print("64x64 droplet parity", errs)
 
 
 def test_mass_and_pressure_jump_fp64():
