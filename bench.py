@@ -368,14 +368,16 @@ def run_batched(args):
     solvers = make()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    failed_seq = 0
+    ok_seq = []
     for s in solvers:
         try:
             s.step(steps)
+            ok_seq.append(True)
         except lbm.LbmError:
-            failed_seq += 1
+            ok_seq.append(False)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
+    failed_seq = ok_seq.count(False)
     for s in solvers:
         s.close()
     # batched
@@ -393,16 +395,21 @@ def run_batched(args):
     b.close()
     for s in solvers:
         s.close()
-    value = nodes * steps / t_batch / 1e6
+    # only solves that finished every step are credited (a solve that went
+    # unphysical is not counted in either arm)
+    nodes_ok = sum(sp["nz"] * sp["nr"] for sp, st in zip(specs, status) if st == lbm.OK)
+    nodes_ok_seq = sum(sp["nz"] * sp["nr"] for sp, ok in zip(specs, ok_seq) if ok)
+    value = nodes_ok * steps / t_batch / 1e6
     print(json.dumps({
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
         "ms_per_step": t_batch * 1e3 / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "256 droplets, log-uniform 64x32..512x256, one launch per step", "solves": 256,
-                   "nodes": nodes, "tuning_strip_grid": list(tuning)},
-        "one_at_a_time": {"value": nodes * steps / t_seq / 1e6, "unit": "MLUPS", "wall_s": t_seq,
+                   "nodes": nodes, "nodes_completed": nodes_ok, "tuning_strip_grid": list(tuning),
+                   "credit": "node-steps of solves that finished every step"},
+        "one_at_a_time": {"value": nodes_ok_seq * steps / t_seq / 1e6, "unit": "MLUPS", "wall_s": t_seq,
                           "failed": failed_seq},
-        "speedup_vs_one_at_a_time": t_seq / t_batch,
+        "speedup_vs_one_at_a_time": (nodes_ok * steps / t_batch) / (nodes_ok_seq * steps / t_seq),
         "failed": sum(1 for x in status if x != lbm.OK),
         "gpu_launches": steps,
     }))
