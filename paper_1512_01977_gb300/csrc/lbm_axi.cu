@@ -377,6 +377,8 @@ int lbm_axi_init_device(lbm_axi* h, const double* rho, const double* uz, const d
         e = Ops<double>::init(h->pdd, stored_rho_ref(h), rho, uz, ur, (double*)h->f[0], h->stream);
     }
     h->cur = 0;
+    // a fresh state: clear the sticky error word (the batched kernel skips a solve whose word is set)
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
     // no arrival halves are pending at the start
     for (int q = 0; q < 2 && e == cudaSuccess && h->hb[0]; q++)
         e = cudaMemsetAsync(h->hb[q], 0, 3 * (size_t)h->plane * (h->precision == 32 ? 4 : 8), h->stream);

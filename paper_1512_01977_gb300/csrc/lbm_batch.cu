@@ -330,6 +330,17 @@ int lbm_axi_batch_autotune(lbm_axi_batch* b, int trials, lbm_axi_batch_tuning* c
     float best = -1.f;
     lbm_axi_batch_tuning bt = {b->strip, b->grid};
     const int strips[2] = {lbm::kStripNarrow, lbm::kStripWide};
+    // the solves' error words before the trials (trial results are discarded; a
+    // solve that had already failed stays failed, and skipped, afterwards)
+    if (cudaMemcpyAsync(b->h_err, b->d_err, sizeof(int) * b->n, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    std::vector<int> err0;
+    try {
+        err0.assign(b->h_err, b->h_err + b->n);
+    } catch (...) {
+        return LBM_ERR_OOM;
+    }
     for (int si = 0; si < 2; si++) {
         const int strip = strips[si];
         const int resident = b->precision == 32 ? Ops<float>::batch_resident_ctas(strip)
@@ -349,7 +360,8 @@ int lbm_axi_batch_autotune(lbm_axi_batch* b, int trials, lbm_axi_batch_tuning* c
     }
     if (best < 0) return LBM_ERR_CUDA;
     if (lbm_axi_batch_set_tuning(b, &bt) != LBM_OK) return LBM_ERR_CUDA;
-    if (cudaMemsetAsync(b->d_err, 0, sizeof(int) * b->n, b->stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(b->d_err, err0.data(), sizeof(int) * b->n, cudaMemcpyHostToDevice, b->stream) !=
+            cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return LBM_ERR_CUDA;
     if (chosen) *chosen = bt;

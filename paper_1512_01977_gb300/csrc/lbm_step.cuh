@@ -883,6 +883,7 @@ __global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB)
                  int parity, int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Params<R> sp;
+    __shared__ int skip;  // the solve already went unphysical: its populations are void, leave them
     const long long total = start[nsolves];
     const long long per = (total + gridDim.x - 1) / gridDim.x;
     long long a = (long long)blockIdx.x * per;
@@ -896,16 +897,21 @@ __global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB)
         }
         const int s = lo;
         __syncthreads();  // everyone is done with the previous segment's parameters
-        if (threadIdx.x == 0) sp = solves[s].p;
-        __syncthreads();
+        if (threadIdx.x == 0) {
+            sp = solves[s].p;
+            skip = *static_cast<volatile const int*>(err + s);
+        }
+        __syncthreads();  // parameters and the skip decision are the same for the whole CTA
         const long long off = a - start[s];
         const int strip = (int)(off / sp.nr), j0 = (int)(off - (long long)strip * sp.nr);
         const int jend = (int)min((long long)sp.nr, j0 + (b - a));
         const R* fin = parity ? solves[s].f_b : solves[s].f_a;
         R* fo = parity ? const_cast<R*>(solves[s].f_a) : solves[s].f_b;
-        int bad = 0;
-        march_cp<R, TZ, RR, CP, MP, AX>(sp, fin, fo, strip, j0, jend, smem_raw, bad);
-        if (bad) atomicOr(&err[s], bad);
+        if (!skip) {
+            int bad = 0;
+            march_cp<R, TZ, RR, CP, MP, AX>(sp, fin, fo, strip, j0, jend, smem_raw, bad);
+            if (bad) atomicOr(&err[s], bad);
+        }
         a += jend - j0;
     }
 }

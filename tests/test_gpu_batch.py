@@ -149,3 +149,34 @@ def test_batch_rejects_mismatched_solves(lbm):
             lbm.Batch(group)
     for s in (a, f32, thin):
         s.close()
+
+
+def test_failed_solve_stays_failed_and_skipped(lbm):
+    """Once a solve goes unphysical the batched kernel leaves it alone: its
+    status stays failed through further steps and an autotune (whose trial
+    launches do not clear it), and the other solves keep their alone results
+    bit for bit."""
+    mix = _mix(seed=8, n=3)
+    refs = []
+    for c, fields, _ in mix:
+        s = c.solver().init(*fields)
+        s.step(40)
+        refs.append(s.moments()["rho"])
+        s.close()
+    solvers = [c.solver().init(*fields) for c, fields, _ in mix]
+    bad_c = Case(40, 20)
+    rho = np.full((20, 40), 0.2)
+    rho[5, 7] = -0.1
+    bad = bad_c.solver().init(rho)
+    b = lbm.Batch([bad] + solvers)
+    assert b.step(10) == lbm.ERR_UNPHYSICAL
+    b.autotune(trials=2)
+    assert b.status()[0] == lbm.ERR_UNPHYSICAL
+    b.step(30)
+    st = b.status()
+    assert st[0] == lbm.ERR_UNPHYSICAL and st[1:] == [lbm.OK] * 3
+    for s, r in zip(solvers, refs):
+        np.testing.assert_array_equal(s.moments()["rho"], r)
+    b.close()
+    for s in solvers + [bad]:
+        s.close()
