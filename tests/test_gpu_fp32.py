@@ -147,3 +147,20 @@ def test_laplace_pressure_fp32():
     print("FP32 Laplace: dp FP64 %.6e FP32 %.6e rel %.2e; M_r drift FP64 %.1e FP32 %.1e" %
           (out[64][0], out[32][0], e_dp, out[64][1], out[32][1]))
     assert e_dp <= 1e-2 and e_m <= 5e-5
+
+
+@pytest.mark.parametrize("nz,nr", [(101, 37), (97, 40)])
+@pytest.mark.parametrize("top", [O.TOP_FREESLIP, O.TOP_NOSLIP, O.TOP_PERIODIC])
+def test_fused_fp32_boundaries_and_odd_widths(top, nz, nr):
+    """The FP32 fused step (two columns per thread) on odd grid widths -- node
+    pairs straddling the periodic z wrap, a ragged last strip -- with each top
+    boundary (periodic top with the axis terms off), against the oracle after
+    300 steps: the droplet bars."""
+    c = Case(nz, nr, top=top, axis=0 if top == O.TOP_PERIODIC else 1)
+    rv, rl = c.coexistence()
+    rho, uz, ur = I.droplet(nz, nr, 12, rl, rv)
+    _, vz, vr = I.random_state(nz, nr, 1.0, 0.0, 2e-3, 41)
+    fields = (rho, vz, vr * (np.arange(nr) + 0.5)[:, None] / nr)
+    e = _errors(c, fields, 300, rho_ref=rv)
+    print("FP32 fused", nz, nr, top, e)
+    assert e["rho"] <= 2e-4 and e["u"] <= 1e-3 and e["p"] <= 1e-3, e
