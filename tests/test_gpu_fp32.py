@@ -164,3 +164,25 @@ def test_fused_fp32_boundaries_and_odd_widths(top, nz, nr):
     e = _errors(c, fields, 300, rho_ref=rv)
     print("FP32 fused", nz, nr, top, e)
     assert e["rho"] <= 2e-4 and e["u"] <= 1e-3 and e["p"] <= 1e-3, e
+
+
+def test_fused_fp32_row_chunks_and_split_path():
+    """FP32: the fused step cut into row chunks (the single-solve autotuner's
+    other fused forms, a separately compiled kernel) agrees with the
+    balanced-wave result within 1e-6 -- a node's arithmetic does not depend
+    on where the rows are cut, only the compiled form's rounding may; the
+    two-kernel path meets the droplet bars against the oracle."""
+    from paper_1512_01977_gb300 import lbm
+
+    c = Case(150, 70)
+    rv, rl = c.coexistence()
+    rho, _, _ = I.droplet(150, 70, 20, rl, rv)
+    _, vz, vr = I.random_state(150, 70, 1.0, 0.0, 2e-3, 43)
+    fields = (rho, vz, vr * (np.arange(70) + 0.5)[:, None] / 70)
+    ref = run_gpu(c, fields, 200, precision=32, rho_ref=rv).moments()
+    for tuning in ((lbm.PATH_FUSED, 16), (lbm.PATH_FUSED, 23), (lbm.PATH_FUSED, 64)):
+        m = run_gpu(c, fields, 200, precision=32, rho_ref=rv, tuning=tuning).moments()
+        assert rel_err(m["rho"], ref["rho"]) <= 1e-6 and vel_err(m, ref) <= 1e-6, tuning
+    ms = run_gpu(c, fields, 200, precision=32, rho_ref=rv, tuning=(lbm.PATH_SPLIT, 0)).moments()
+    mo = run_oracle(c, fields, 200).moments()
+    assert rel_err(ms["rho"], mo["rho"]) <= 2e-4 and vel_err(ms, mo) <= 1e-3
