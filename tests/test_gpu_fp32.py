@@ -186,3 +186,44 @@ def test_fused_fp32_row_chunks_and_split_path():
     ms = run_gpu(c, fields, 200, precision=32, rho_ref=rv, tuning=(lbm.PATH_SPLIT, 0)).moments()
     mo = run_oracle(c, fields, 200).moments()
     assert rel_err(ms["rho"], mo["rho"]) <= 2e-4 and vel_err(ms, mo) <= 1e-3
+
+
+def test_maximum_grid_sampled_windows():
+    """The largest grid a solve accepts, nz * nr = 2^27 nodes (16384 x 8192,
+    FP32: 9.7 GB of populations), where plane offsets come within a factor of
+    two of the 32-bit index range: after 2 steps, windows across the periodic
+    z seam at the axis, deep in the bulk and at the top match the oracle
+    (the domain-of-dependence argument of the full-size wave test).  One more
+    row is refused."""
+    from paper_1512_01977_gb300 import lbm
+
+    nz, nr, n_steps = 16384, 8192, 2
+    c = Case(nz, nr, T_over_Tc=0.9, tau=0.6)
+    _, rho0 = c.coexistence()
+    with pytest.raises(lbm.LbmError) as e:
+        Case(nz, nr + 1, T_over_Tc=0.9, tau=0.6).solver(precision=32, rho_ref=rho0)
+    assert e.value.code == lbm.ERR_INVALID_ARG
+    rho, uz, ur = I.density_wave(nz, nr, rho0)
+    s = c.solver(precision=32, rho_ref=rho0)
+    s.init(rho, uz, ur)
+    s.step(n_steps)
+    mg = s.moments()
+    s.close()
+    m = 7 * n_steps + 8
+    wz, wr = 40, 32
+    for (k0, j0, at_axis, at_top) in ((nz - 20, 0, True, False), (12000, 6000, False, False),
+                                      (9000, nr - wr, False, True)):
+        ks = np.arange(k0 - m, k0 + wz + m) % nz
+        lo = 0 if at_axis else j0 - m
+        hi = nr if at_top else j0 + wr + m
+        sub = lambda a: np.ascontiguousarray(a[lo:hi][:, ks])  # noqa: E731
+        wc = Case(len(ks), hi - lo, T_over_Tc=0.9, tau=0.6, r0=float(lo))
+        o = O.Oracle(wc.oracle_params()).init(sub(rho), sub(uz), sub(ur))
+        o.step(n_steps)
+        mo = o.moments()
+        inner = (slice(0, wr) if at_axis else (slice(m, m + wr) if not at_top else slice(m, None)),
+                 slice(m, m + wz))
+        g = {k: mg[k][lo:hi][:, ks][inner] for k in ("rho", "uz", "ur", "p")}
+        r = {k: mo[k][inner] for k in ("rho", "uz", "ur", "p")}
+        assert rel_err(g["rho"], r["rho"]) <= 1e-6
+        assert vel_err(g, r) <= 1e-4
