@@ -54,7 +54,22 @@ def _args():
                          "continuous batching vs a one-at-a-time server")
     ap.add_argument("--requests", type=int, default=48, help="served: requests per arrival rate")
     ap.add_argument("--budget-mb", type=int, default=4096, help="served: HBM admission budget")
-    return ap.parse_args()
+    ap.add_argument("--grid", default="%dx%d" % (NZ, NR),
+                    help="wave: nz x nr of the wave (the default is the headline workload; other sizes are "
+                         "for profiling)")
+    ap.add_argument("--path", default="fused", choices=["fused", "split"],
+                    help="wave: the single-pass kernel (default) or the two-kernel path")
+    args = ap.parse_args()
+    _set_grid(args.grid)
+    return args
+
+
+def _set_grid(spec):
+    global NZ, NR, WORKLOAD
+    nz, nr = (int(x) for x in spec.lower().split("x"))
+    if (nz, nr) != (NZ, NR):
+        NZ, NR = nz, nr
+        WORKLOAD = "density wave %dx%d, CS T=0.9Tc, tau=0.6, A=-0.152, FP32 deviation storage" % (NZ, NR)
 
 
 def _dist():
@@ -243,6 +258,8 @@ def run_ours(args):
 
     stream = torch.cuda.Stream()
     s = lbm.Solver(NZ, NR, TAU, eos=eos, A=A, precision=32, rho_ref=rho0, stream=stream.cuda_stream)
+    if args.path == "split":
+        lbm.lbm_axi_set_tuning(s.h, lbm.PATH_SPLIT, 0)
     s.init(*h_in)
     lbm.lbm_axi_step(s.h, args.warmup)
 
@@ -280,7 +297,7 @@ def run_ours(args):
     # fused path: one launch does the whole step, so its algorithmic bytes are the step's 140 B/node
     bytes_main = BYTES_STEP if path == lbm.PATH_FUSED else BYTES_B
     ach_b = bytes_main * n / t_b / 1e9
-    traffic = _ncu_traffic()
+    traffic = _ncu_traffic() if path == lbm.PATH_FUSED else None  # the committed counters are the fused kernel's
 
     # ---- end to end through the C ABI: pinned host -> init -> K steps -> moments -> pinned host
     barrier()
@@ -297,6 +314,7 @@ def run_ours(args):
     mass_rw, _ = s.mass()
     s.close()
 
+    pop_mb = int(round(9 * n * 4 / 1e6))
     if rank == 0:
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
@@ -306,7 +324,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "nz": NZ, "nr": NR, "nodes": n, "replicas": ws,
-                       "l2": "no flush: inputs larger than L2 (2 x 302 MB FP32 population buffers)",
+                       "l2": ("no flush: inputs larger than L2 (2 x %d MB FP32 population buffers)" % pop_mb)
+                       if 2 * pop_mb > 129 else "inputs smaller than L2 (%d MB): not an HBM measurement" % (2 * pop_mb),
                        "parallelism": "replicas only (independent solves per GPU)",
                        "device": props.name},
             "roofline": {"bound": "hbm",
