@@ -304,3 +304,75 @@ def test_fig2_coexistence_curve(lbm):
         el, ev, _ = _slab_coexistence(lbm, T, 0.0)
         print("Fig. 2 A = 0, T %.2f: liquid %+.2e, vapour %+.2e of Maxwell" % (T, el, ev))
         assert ev < -2e-2
+
+
+def _oscillation_vdw(lbm, kappa, tau=0.8, A=0.0, T=0.8, shape=(62, 76), steps=25000, every=100):
+    """Mode-2 frequency of an ellipsoidal drop with the paper's vdW fluid
+    (lambda = 0.01, A = 0, T = 0.8 T_c, density ratio about 9; tau = 0.8, the
+    smallest at which this drop runs from rest, the paper's being 0.7), and the
+    Miller-Scriven value for its measured radius and densities.  At this ratio
+    the large vapour volume of the 500 x 250 box evaporates a drop started at
+    the flat-interface densities (R 66 -> 46), so a first static run measures
+    the 1/R (Kelvin) shift of both densities and the drop starts from the
+    densities it has at its own radius."""
+    nz, nr = 500, 250
+    eos = lbm.make_eos(lbm.EOS_VDW, T, lam=LAM)
+    rv0, rl0 = lbm.lbm_eos_coexistence(eos)
+    s = lbm.Solver(256, 16, tau, eos=eos, A=A, precision=64, top=lbm.TOP_PERIODIC, axis=0)
+    s.init(*I.slab(256, 16, rl0, rv0, width=4.0), physical=True)
+    s.step(40000)
+    m = s.moments()["rho"]
+    lv, ll = float(m[:, 0].mean()), float(m[:, 128].mean())
+    s.close()
+    s = lbm.Solver(320, 320, tau, eos=eos, A=A, precision=64, top=lbm.TOP_PERIODIC, axis=0)
+    s.init(*I.droplet_2d(320, 320, 64, ll, lv), physical=True)
+    s.step(30000)
+    R2, _, _ = _plane_state(s.moments()["rho"])
+    sig2d = s.pressure_jump(160, 160, R2 / 2, R2 + 12) * R2
+    s.close()
+    Ra, Rz = shape
+    R0 = (Ra * Ra * Rz) ** (1 / 3)
+    s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=64, kappa=kappa)
+    s.init(*I.droplet(nz, nr, R0, ll, lv), physical=True)
+    s.step(20000)
+    R1, rl1, rv1 = _axis_state(s.moments()["rho"])
+    s.close()
+    s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=64, kappa=kappa)
+    s.init(*I.droplet(nz, nr, R0, ll + (rl1 - ll) * R1 / R0, lv + (rv1 - lv) * R1 / R0), physical=True)
+    s.step(20000)
+    Rs, rl, rv = _axis_state(s.moments()["rho"])
+    s.close()
+    k = Rs / R0
+    s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=64, kappa=kappa)
+    s.init(*I.ellipsoid(nz, nr, Ra * k, Rz * k, rl, rv), physical=True)
+    ts, ext, rad, dens = [], [], [], []
+    for i in range(steps // every):
+        rho = lbm.lbm_axi_moments(s.h, nz, nr, want=("rho",))["rho"]
+        R, a, b = _axis_state(rho)
+        ts.append(i * every)
+        ext.append(_half_extent(rho[0], a, b))
+        rad.append(R)
+        dens.append((a, b))
+        s.step(every)
+    s.close()
+    ts, ext = np.array(ts[3:]), np.array(ext[3:])
+    Rm = float(np.mean(rad[3:]))
+    rlm, rvm = np.mean([d[0] for d in dens[3:]]), np.mean([d[1] for d in dens[3:]])
+    nu = (tau - 0.5) / 3
+    w_ms = O.analytic.miller_scriven_omega2(sig2d, Rm, rlm, rvm, nu, nu)
+    w, c = O.analytic.fit_damped_cosine(ts, ext, w_guess=w_ms)
+    return dict(omega=w, omega_ms=w_ms, err=w / w_ms - 1, R=Rm, R_flat_start=R1, R_equilibrated=Rs)
+
+
+def test_mode2_oscillation_vdw(lbm):
+    """The paper's fluid (vdW, A = 0, ratio about 9): with c_s^4 in F_axis the
+    mode-2 frequency is Miller-Scriven's within 5 %; with the paper's c_k^4 it
+    is 3-15 % low (measured -9 %; the paper reports 6-8 % errors)."""
+    out = {}
+    for kappa in (lbm.KAPPA_LATTICE, lbm.KAPPA_THERMO):
+        r = _oscillation_vdw(lbm, kappa)
+        out[kappa] = r
+        print("mode 2 vdW, kappa %d: omega %.4e MS %.4e err %+.4f R %.2f (flat-density start %.1f, equilibrated %.1f)"
+              % (kappa, r["omega"], r["omega_ms"], r["err"], r["R"], r["R_flat_start"], r["R_equilibrated"]))
+    assert abs(out[lbm.KAPPA_LATTICE]["err"]) <= 0.05
+    assert -0.15 <= out[lbm.KAPPA_THERMO]["err"] <= -0.03
