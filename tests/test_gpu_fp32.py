@@ -227,3 +227,23 @@ def test_maximum_grid_sampled_windows():
         r = {k: mo[k][inner] for k in ("rho", "uz", "ur", "p")}
         assert rel_err(g["rho"], r["rho"]) <= 1e-6
         assert vel_err(g, r) <= 1e-4
+
+
+def test_link_midpoint_source_fp32():
+    """h_eval = LINK_AVG on the two-kernel path in FP32 (rho_ref = rho_v)
+    against the oracle's link average, droplet from rest with a random flow,
+    300 steps: the droplet bars."""
+    c = Case(64, 48, h_eval=O.H_LINK_AVG)
+    rv, rl = c.coexistence()
+    rho, _, _ = I.droplet(64, 48, 14, rl, rv)
+    _, vz, vr = I.random_state(64, 48, 1.0, 0.0, 2e-3, 44)
+    fields = (rho, vz, vr * (np.arange(48) + 0.5)[:, None] / 48)
+    o = O.Oracle(c.oracle_params()).init(*fields, physical=True).step(300)
+    s = c.solver(32, rv).init(*fields, physical=True).step(300)
+    mo, mg = o.moments(), s.moments()
+    mr, _ = s.mass()
+    s.close()
+    e = {"rho": rel_err(mg["rho"], mo["rho"]), "u": vel_err(mg, mo), "p": rel_err(mg["p"], mo["p"]),
+         "mass": abs(mr / o.mass_rweighted() - 1)}
+    print("FP32 link-midpoint errors", e)
+    assert e["rho"] <= 2e-4 and e["u"] <= 1e-3 and e["p"] <= 1e-3 and e["mass"] <= 2e-5, e
