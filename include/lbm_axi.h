@@ -174,8 +174,10 @@ int lbm_axi_time_kernels(lbm_axi* h, long long n, double* ms);
  *   rows_per_cta: 0 -- one wave of CTAs, each marching an equal share of the
  *         (z-strip, row) space (default); > 0 -- fixed chunks of that many rows
  *         of one z-strip per CTA.
- * The default is FUSED (nr >= 16) with rows_per_cta = 0.  The paths agree to
- * rounding.  Setting waits for the handle's stream. */
+ * The default is FUSED (nr >= 16) with rows_per_cta = 0; a solve with
+ * h_eval = LBM_H_LINK_AVG is SPLIT only.  The paths agree to rounding.
+ * Setting waits for the handle's stream; it returns LBM_ERR_INVALID_ARG for an
+ * unknown path, rows_per_cta < 0, or FUSED when nr < 16 or with LBM_H_LINK_AVG. */
 enum { LBM_PATH_FUSED = 1, LBM_PATH_SPLIT = 2 };
 typedef struct {
     int path;
