@@ -87,7 +87,8 @@ def test_ring_schedule(rr):
 
 
 def test_too_shallow_rings_are_caught():
-    """The emulation has teeth: one slot fewer in the rho / j ring breaks it."""
+    """The emulation has teeth: the next smaller power-of-two depth of the
+    rho / j ring (the kernel masks ring indices) breaks it."""
     d = _depths(2)
     shallow = dict(d, DJ=8)
     with pytest.raises(AssertionError):
