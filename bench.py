@@ -31,10 +31,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 NZ, NR, TAU, A, T_OVER_TC = 4096, 2048, 0.6, -0.152, 0.9
-# Algorithmic bytes per node and time step, FP32 (the roofline figure): the two-kernel form of the
-# step reads 9 populations and writes rho, j_z, j_r, psi (52 B), then reads 9 populations and the 4
-# fields and writes 9 populations (88 B): 140 B.  The fused kernel needs only the population floor,
-# 9 reads + 9 writes = 72 B, which is reported beside it.
+# Algorithmic bytes per node and time step, FP32.  The fused kernel (the default path) reads and
+# writes the 9 populations: 72 B, its roofline figure.  The two-kernel form of the step reads 9
+# populations and writes rho, j_z, j_r, psi (52 B), then reads 9 populations and the 4 fields and
+# writes 9 populations (88 B): 140 B, reported beside it as the equivalent two-kernel traffic.
 BYTES_STEP = 140
 BYTES_FUSED = 72
 BYTES_B = 88
@@ -48,6 +48,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-blocks", dest="blocks", action="store_false",
+                    help="wave: leave out the bounded batched and served blocks of the default line")
     ap.add_argument("--workload", default="wave", choices=["wave", "batched", "served"],
                     help="wave: the 4096x2048 density wave (headline); batched: 256 uneven droplets in one "
                          "launch per step vs one solve at a time; served: Poisson request stream with "
@@ -132,55 +134,106 @@ def _ncu_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    """SM clocks, power and clock-event (throttle) reasons of the bench's GPU,
+    read (never set) through NVML every `period` seconds from a background
+    thread; nvidia-smi polling is the fallback when NVML cannot be loaded.
+    Samples are tagged with the phase the caller marks (e.g. the timed region)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+             0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index):
-        self.index = index
-        self.proc = None
+    def __init__(self, device_index, period=0.002):
+        import threading
+
+        self.period = period
+        self.samples = []  # (phase, sm_mhz, sm_max_mhz, power_w, reasons bitmask)
+        self.phase = "idle"
+        self._stop = threading.Event()
+        self._thread = None
+        self._nvml = None
+        self._dev = None
+        self.source = None
+        self._open_nvml(device_index)
+
+    def _open_nvml(self, device_index):
+        import ctypes as C
+
+        try:
+            import torch
+
+            nv = C.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return
+            dev = C.c_void_p()
+            props = torch.cuda.get_device_properties(device_index)
+            ok = False
+            uid = str(getattr(props, "uuid", "") or "")
+            for cand in (uid, "GPU-" + uid):
+                if uid and nv.nvmlDeviceGetHandleByUUID(cand.encode(), C.byref(dev)) == 0:
+                    ok = True
+                    break
+            if not ok and hasattr(props, "pci_bus_id"):
+                bus = "%08x:%02x:%02x.0" % (getattr(props, "pci_domain_id", 0), props.pci_bus_id,
+                                            getattr(props, "pci_device_id", 0))
+                ok = nv.nvmlDeviceGetHandleByPciBusId_v2(bus.encode(), C.byref(dev)) == 0
+            if ok:
+                self._nvml, self._dev, self.source = nv, dev, "nvml"
+        except (OSError, AttributeError, ImportError):
+            self._nvml = None
+
+    def _read_nvml(self):
+        import ctypes as C
+
+        nv, dev = self._nvml, self._dev
+        sm, smax, mw, rs = C.c_uint(), C.c_uint(), C.c_uint(), C.c_ulonglong()
+        if nv.nvmlDeviceGetClockInfo(dev, 1, C.byref(sm)) != 0:
+            return None
+        nv.nvmlDeviceGetMaxClockInfo(dev, 1, C.byref(smax))
+        nv.nvmlDeviceGetPowerUsage(dev, C.byref(mw))
+        fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        fn(dev, C.byref(rs))
+        return float(sm.value), float(smax.value), mw.value / 1000.0, int(rs.value)
+
+    def _loop(self):
+        while not self._stop.is_set():
+            r = self._read_nvml()
+            if r is not None:
+                self.samples.append((self.phase,) + r)
+            self._stop.wait(self.period)
 
     def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
-                                         stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.proc = None
+        import threading
+
+        if self._nvml is not None:
+            self._thread = threading.Thread(target=self._loop, daemon=True)
+            self._thread.start()
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
-        if self.proc:
-            self.proc.terminate()
-            try:
-                out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        self._stop.set()
+        if self._thread is not None:
+            self._thread.join(timeout=5)
 
-    def summary(self):
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in getattr(self, "lines", []):
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for name, val in zip(names, parts[5:9]):
-                if val.lower().startswith("active"):
+    def mark(self, phase):
+        self.phase = phase
+        if self._nvml is not None:  # one sample at every phase change
+            r = self._read_nvml()
+            if r is not None:
+                self.samples.append((phase,) + r)
+
+    def summary(self, phases):
+        rows = [x for x in self.samples if x[0] in phases]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "source": self.source}
+        reasons = set()
+        for x in rows:
+            for bit, name in self.NAMES.items():
+                if x[4] & bit:
                     reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(x[1] for x in rows), "sm_max_mhz": max(x[2] for x in rows),
+                "power_w_max": max(x[3] for x in rows), "reasons": sorted(reasons), "samples": len(rows),
+                "source": self.source}
 
 
 def _wave_fields(nz, nr, rho0):
@@ -189,42 +242,72 @@ def _wave_fields(nz, nr, rho0):
     return I.density_wave(nz, nr, rho0, amp=0.01, noise=1e-4, seed=20151201)
 
 
-def _cpu_baseline(rho0, steps=4):
-    """The FP64 oracle, as it stands, on the full grid for a few steps (1 core)."""
+def _oracle_rate(nz, nr, rho0, steps, threads):
+    """Node updates per second of the FP64 oracle, as it stands, on an nz x nr
+    window of the workload (OpenMP timing build; `threads` host threads)."""
     import oracle as O
+    from oracle import core
 
-    p = O.make_params(NZ, NR, TAU, O.EOS_CS, T_OVER_TC, A=A, top=O.TOP_FREESLIP)
-    o = O.Oracle(p).init(*_wave_fields(NZ, NR, rho0))
+    p = O.make_params(nz, nr, TAU, O.EOS_CS, T_OVER_TC, A=A, top=O.TOP_FREESLIP)
+    o = O.Oracle(p, omp=True).init(*_wave_fields(nz, nr, rho0))
+    used = core.threads(threads)
+    o.step(1)  # first touch of the work arrays
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
-    return {"value": NZ * NR * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "%d steps of the full %dx%d grid, FP64, single thread (%.1f s)" % (steps, NZ, NR, dt)}
+    return nz * nr * steps / dt, used, dt
+
+
+def _cpu_baseline(rho0):
+    """The FP64 oracle timed on this host: all cores and one core, on a
+    bounded sample of the workload (the full grid for a few steps)."""
+    n_all = os.cpu_count() or 1
+    r_all, used_all, dt_all = _oracle_rate(NZ, NR, rho0, 6, n_all)
+    r_one, _, dt_one = _oracle_rate(NZ, NR, rho0, 2, 1)
+    from oracle import core
+
+    core.threads(n_all)
+    return {"value": r_all / 1e6, "unit": "MLUPS", "cores": used_all, "kind": "oracle",
+            "sample": "6 steps of the full %dx%d grid, FP64, OpenMP over %d threads (%.1f s)"
+                      % (NZ, NR, used_all, dt_all),
+            "nproc": n_all,
+            "one_core": {"value": r_one / 1e6, "unit": "MLUPS", "cores": 1,
+                         "sample": "2 steps of the full grid, one thread (%.1f s)" % dt_one}}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle on a 256 x 256 window of the workload."""
+    """Reference arm: the FP64 CPU oracle, as it stands, on all host cores, on
+    a window of the workload sized so the K timed steps stay bounded."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     import oracle as O
 
-    nz, nr = 256, 256
+    # each step a sample: the full grid for K <= 20, smaller windows (same
+    # aspect, same recipe) for longer runs, so the run stays within ~a minute
+    scale = min(1.0, 20.0 / max(1, args.steps))
+    nz = max(64, int(NZ * scale ** 0.5) // 32 * 32)
+    nr = max(32, int(NR * scale ** 0.5) // 32 * 32)
     p = O.make_params(nz, nr, TAU, O.EOS_CS, T_OVER_TC, A=A, top=O.TOP_FREESLIP)
     rho0 = O.eos.maxwell_densities(p)[1]
-    o = O.Oracle(p).init(*_wave_fields(nz, nr, rho0))
-    o.step(args.warmup)
+    n_all = os.cpu_count() or 1
+    from oracle import core
+
+    o = O.Oracle(p, omp=True).init(*_wave_fields(nz, nr, rho0))
+    used = core.threads(n_all)
+    o.step(max(1, args.warmup))
     t0 = time.perf_counter()
     o.step(args.steps)
     dt = time.perf_counter() - t0
     v = nz * nr * args.steps / dt / 1e6
-    sample = "%dx%d window of the workload (same EOS, tau, A, wave recipe), FP64, single thread" % (nz, nr)
+    sample = ("%dx%d window of the workload (same EOS, tau, A, wave recipe), FP64, OpenMP over %d threads"
+              % (nz, nr, used))
     print(json.dumps({
         "impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD + " (oracle window %dx%d)" % (nz, nr), "nz": nz, "nr": nr},
-        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -268,16 +351,28 @@ def run_ours(args):
 
     # ---- device-timed throughput: K steps, inputs resident in HBM
     props = torch.cuda.get_device_properties(local)
-    smi_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if ws >= 1 else str(local)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    with ClockSampler(smi_index) as clk:
+    clk = ClockSampler(local)
+    with clk:
+        barrier()
+        clk.mark("timed")
         e0.record(stream)
         lbm.lbm_axi_step_async(s.h, args.steps)
         e1.record(stream)
         e1.synchronize()
-    lbm.lbm_axi_sync(s.h)
-    barrier()
+        clk.mark("after")
+        lbm.lbm_axi_sync(s.h)
+        barrier()
+        # a clock window: the same step loop for at least 0.5 s after the timed
+        # region (not part of any figure), so that the clock record holds enough
+        # samples even when the timed region lasts a few milliseconds
+        clk.mark("window")
+        w0 = time.perf_counter()
+        n_window = 0
+        while time.perf_counter() - w0 < 0.5:
+            lbm.lbm_axi_step(s.h, 200)
+            n_window += 200
+        clk.mark("done")
     ms = e0.elapsed_time(e1)
     ms_max = rep.max(ms)
     value = replicas.aggregate_rate(n * args.steps, ws, ms_max * 1e-3) / 1e6  # MLUPS
@@ -294,8 +389,9 @@ def run_ours(args):
         # launch duration over that region is the region's time per step
         t_a, t_b = 0.0, t_step
     peak, peak_kind = _peaks()
-    # fused path: one launch does the whole step, so its algorithmic bytes are the step's 140 B/node
-    bytes_main = BYTES_STEP if path == lbm.PATH_FUSED else BYTES_B
+    # algorithmic bytes of the kernel that ran: the fused kernel reads and writes the
+    # 9 populations (72 B/node); kernel (b) of the split path 88 B/node
+    bytes_main = BYTES_FUSED if path == lbm.PATH_FUSED else BYTES_B
     ach_b = bytes_main * n / t_b / 1e9
     traffic = _ncu_traffic() if path == lbm.PATH_FUSED else None  # the committed counters are the fused kernel's
 
@@ -315,10 +411,21 @@ def run_ours(args):
     s.close()
 
     pop_mb = int(round(9 * n * 4 / 1e6))
+    extra = {}
+    if ws == 1 and args.blocks:
+        # the batched and served workloads, bounded, on the same GPU after the headline
+        extra["batched"] = _batched_block(steps=200, warmup=3)
+        extra["served"] = _served_block(rates=(100,), requests=24, budget_mb=4096)
     if rank == 0:
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
             cpu = _cpu_baseline(rho0)
+        timed = clk.summary({"timed", "after"})
+        window = clk.summary({"window"})
+        clocks = dict(timed if timed["samples"] >= 3 else window)
+        clocks.update({"samples_timed_region": timed["samples"], "samples_window": window["samples"],
+                       "window": "%d more steps of the same loop right after the timed region" % n_window,
+                       "reasons_window": window["reasons"], "sm_mhz_window": window["sm_mhz"]})
         out = {
             "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -333,44 +440,46 @@ def run_ours(args):
                          if path == lbm.PATH_FUSED else "k_update (forces+EDM+source+collide)",
                          "achieved": ach_b, "peak": peak, "unit": "GB/s", "frac": ach_b / peak,
                          "peak_source": peak_kind, "traffic": traffic,
-                         "algorithmic_bytes_per_node": bytes_main, "avg_launch_us": t_b * 1e6,
+                         "algorithmic_bytes_per_node": bytes_main,
+                         "traffic_bytes_per_node": traffic / n if traffic else None,
+                         "avg_launch_us": t_b * 1e6,
                          "avg_launch_source": "timed region / launches" if path == lbm.PATH_FUSED
                          else "CUDA events around each launch",
                          "isolated_launch_us": t_iso * 1e6,
                          "launches_per_step": 1 if path == lbm.PATH_FUSED else 2,
-                         "kernel_floor_bytes_per_node": BYTES_FUSED,
-                         "kernel_floor_frac": BYTES_FUSED * n / t_step / 1e9 / peak,
-                         "step_frac": BYTES_STEP * n / t_step / 1e9 / peak,
+                         "frac_of_nominal_7900_gbs": ach_b / 7900.0,
+                         "two_kernel_equivalent": {
+                             "bytes_per_node": BYTES_STEP,
+                             "frac": BYTES_STEP * n / t_step / 1e9 / peak,
+                             "note": "the traffic the two-kernel form of the step would need at this step time"},
                          "rows_per_cta": rows_per_cta},
-            "e2e": {"value": e2e, "unit": "MLUPS", "h2d_bytes_per_step": 3 * 8 * n / args.steps,
+            "e2e": {"value": e2e, "unit": "MLUPS", "steps": args.steps, "h2d_bytes_per_step": 3 * 8 * n / args.steps,
                     "d2h_bytes_per_step": 4 * 8 * n / args.steps,
-                    "note": "one solve: init from pinned host fields, K steps, moments back to pinned host"},
+                    "note": "one solve: init from pinned host fields, K steps, moments back to pinned host; "
+                            "the copies are fixed per run, so the rate rises with K"},
             "gpu_launches": (1 if path == lbm.PATH_FUSED else 2) * args.steps,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "mass_rweighted": mass_rw,
         }
+        out.update(extra)
         if cpu is not None:
             out["cpu_baseline"] = cpu
         print(json.dumps(out))
     rep.close()
 
 
-def run_batched(args):
+def _batched_block(steps, warmup, trials=3):
     """256 independent droplets (sizes log-uniform 64x32 .. 512x256, R = 0.25 of
     the shorter side, T/Tc ~ U[0.5, 0.85], tau ~ U[0.6, 1.0], CS, FP32 with
-    deviations about rho_v, started at rest), `--steps` steps each: one batched launch per step
-    (autotuned) against the same solves stepped one at a time."""
+    deviations about rho_v, started at rest), `steps` steps each: one batched
+    launch per step (autotuned) against the same solves stepped one at a time.
+    Only solves that finish every step are credited, in both arms."""
     import torch
 
-    import __graft_entry__
     from paper_1512_01977_gb300 import inputs as I
     from paper_1512_01977_gb300 import lbm
 
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    __graft_entry__.build()
     specs = I.batch_droplets(n=256, seed=4)
-    steps = args.steps
 
     def make():
         out = []
@@ -396,15 +505,13 @@ def run_batched(args):
             ok_seq.append(False)
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
-    failed_seq = ok_seq.count(False)
     for s in solvers:
         s.close()
     # batched
     solvers = make()
     b = lbm.Batch(solvers)
-    tuning = b.autotune(trials=3)
-    b.step(args.warmup)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tuning = b.autotune(trials=trials)
+    b.step(warmup)
     torch.cuda.synchronize()
     w0 = time.perf_counter()
     b.step_async(steps)
@@ -414,52 +521,73 @@ def run_batched(args):
     b.close()
     for s in solvers:
         s.close()
-    # only solves that finished every step are credited (a solve that went
-    # unphysical is not counted in either arm)
     nodes_ok = sum(sp["nz"] * sp["nr"] for sp, st in zip(specs, status) if st == lbm.OK)
     nodes_ok_seq = sum(sp["nz"] * sp["nr"] for sp, ok in zip(specs, ok_seq) if ok)
     value = nodes_ok * steps / t_batch / 1e6
-    print(json.dumps({
-        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
-        "ms_per_step": t_batch * 1e3 / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "256 droplets, log-uniform 64x32..512x256, one launch per step", "solves": 256,
-                   "nodes": nodes, "nodes_completed": nodes_ok, "tuning_strip_grid": list(tuning),
-                   "credit": "node-steps of solves that finished every step"},
-        "one_at_a_time": {"value": nodes_ok_seq * steps / t_seq / 1e6, "unit": "MLUPS", "wall_s": t_seq,
-                          "failed": failed_seq},
-        "speedup_vs_one_at_a_time": (nodes_ok * steps / t_batch) / (nodes_ok_seq * steps / t_seq),
-        "failed": sum(1 for x in status if x != lbm.OK),
-        "gpu_launches": steps,
-    }))
+    seq = nodes_ok_seq * steps / t_seq / 1e6
+    return {"value": value, "unit": "MLUPS", "steps": steps, "warmup": warmup, "wall_s": t_batch,
+            "workload": "256 droplets, log-uniform 64x32..512x256, CS, T/Tc 0.5..0.85, tau 0.6..1.0, "
+                        "FP32, started at rest; one launch per step (CUDA graph)",
+            "solves": 256, "nodes": nodes, "nodes_completed": nodes_ok, "tuning_strip_grid": list(tuning),
+            "failed": sum(1 for x in status if x != lbm.OK),
+            "credit": "node-steps of solves that finished every step",
+            "one_at_a_time": {"value": seq, "unit": "MLUPS", "wall_s": t_seq, "failed": ok_seq.count(False)},
+            "speedup_vs_one_at_a_time": value / seq if seq > 0 else None,
+            "timing": "host wall clock around the step loop, synchronised on both sides"}
 
 
-def run_served(args):
-    """Poisson request streams (rates 10..1000/s): continuous batching vs one
-    request at a time; p50 / p99 latency and MLUPS per rate."""
+def _served_block(rates, requests, budget_mb):
+    """Poisson request streams: continuous batching vs one request at a time;
+    p50 / p99 latency and MLUPS per rate."""
+    from paper_1512_01977_gb300 import inputs as I
+    from paper_1512_01977_gb300 import serve
+
+    rows = []
+    for rate in rates:
+        reqs = I.request_stream(rate, requests, seed=5)
+        _, st = serve.serve(reqs, budget_bytes=budget_mb << 20)
+        _, sq = serve.serve_sequential(reqs)
+        rows.append({"rate_per_s": rate, "batched": st, "one_at_a_time": sq})
+    return {"workload": "served Poisson stream, droplets + waves, CS/vdW, T/Tc 0.5..0.9, grids 32x32..1024x512, "
+                        "1k..20k steps", "requests_per_rate": requests, "budget_mb": budget_mb, "rates": rows}
+
+
+def run_batched(args):
     import torch
 
     import __graft_entry__
-    from paper_1512_01977_gb300 import inputs as I
-    from paper_1512_01977_gb300 import serve
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     __graft_entry__.build()
-    rows = []
-    for rate in (10, 30, 100, 300, 1000):
-        reqs = I.request_stream(rate, args.requests, seed=5)
-        _, st = serve.serve(reqs, budget_bytes=args.budget_mb << 20)
-        _, sq = serve.serve_sequential(reqs)
-        rows.append({"rate_per_s": rate, "batched": st, "one_at_a_time": sq})
-    best = max(r["batched"]["mlups"] for r in rows)
+    blk = _batched_block(args.steps, args.warmup)
+    print(json.dumps({
+        "metric": "MLUPS", "value": blk["value"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": blk["wall_s"] * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": blk["workload"], "solves": 256, "nodes": blk["nodes"],
+                   "nodes_completed": blk["nodes_completed"], "tuning_strip_grid": blk["tuning_strip_grid"],
+                   "credit": blk["credit"]},
+        "one_at_a_time": blk["one_at_a_time"], "speedup_vs_one_at_a_time": blk["speedup_vs_one_at_a_time"],
+        "failed": blk["failed"], "gpu_launches": args.steps,
+    }))
+
+
+def run_served(args):
+    import torch
+
+    import __graft_entry__
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    blk = _served_block((10, 30, 100, 300, 1000), args.requests, args.budget_mb)
+    best = max(r["batched"]["mlups"] for r in blk["rates"])
     print(json.dumps({
         "metric": "MLUPS", "value": best, "unit": "MLUPS", "n_gpus": 1, "steps": None, "warmup": 0,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "served Poisson stream, droplets + waves, CS/vdW, T/Tc 0.5..0.9, "
-                               "grids 32x32..1024x512, 1k..20k steps", "requests_per_rate": args.requests,
-                   "budget_mb": args.budget_mb},
-        "rates": rows,
+        "config": {"workload": blk["workload"], "requests_per_rate": args.requests, "budget_mb": args.budget_mb},
+        "rates": blk["rates"],
     }))
 
 

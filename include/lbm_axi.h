@@ -87,6 +87,18 @@ enum {
  *                   matching half-step in time. */
 enum { LBM_H_LOCAL = 0, LBM_H_LINK_AVG = 1 };
 
+/* How the force F enters the collision of Eq. (lbm):
+ *   LBM_FORCING_EDM  the exact difference method, S_i = f^eq_i(rho, u0 + F/rho)
+ *                    - f^eq_i(rho, u0), with f^eq at the bare velocity u0 (Sec. II.C,
+ *                    the scheme the Kupershtokh force is defined with; default);
+ *   LBM_FORCING_GUO  Guo forcing (Sec. II.A): f^eq at the fluid velocity
+ *                    u = u0 + F/(2 rho) and S_i = w_i (1 - 1/(2 tau)) [(c_i - u).F / c_s^2
+ *                    + (c_i.u)(c_i.F) / c_s^4] (the printed second term, (c_i - u).(c_i - F),
+ *                    is read as Guo's (c_i.u)(c_i.F)).  Two-kernel path only, like
+ *                    LBM_H_LINK_AVG: the fused path refuses it and such a solve cannot
+ *                    join a batch. */
+enum { LBM_FORCING_EDM = 0, LBM_FORCING_GUO = 1 };
+
 typedef struct {
     int precision;  /* 64: FP64 populations and arithmetic; 32: FP32 populations stored as
                        deviations f_i - w_i rho_ref, FP32 arithmetic, FP64 reductions */
@@ -99,18 +111,21 @@ typedef struct {
     double rho_ref; /* reference density of the FP32 deviation storage (0 allowed) */
     double g_z;     /* constant body acceleration along z (0 in the paper's runs) */
     void* stream;   /* cudaStream_t to run on; NULL: the handle creates its own */
-    int h_eval;     /* LBM_H_*: where h_i of Eq. (lbm) is evaluated (see below) */
+    int h_eval;     /* LBM_H_*: where h_i of Eq. (lbm) is evaluated (see above) */
+    int forcing;    /* LBM_FORCING_*: how F enters the collision (see above) */
 } lbm_axi_opts;
 
 typedef struct lbm_axi lbm_axi;
 
 /* Fill *opts with the defaults: FP64, free-slip top, axis terms and
  * multiphase on, LBM_KAPPA_THERMO, hr_sign -1, rho_ref 0, g_z 0, own stream,
- * LBM_H_LOCAL. */
+ * LBM_H_LOCAL, LBM_FORCING_EDM. */
 void lbm_axi_default_opts(lbm_axi_opts* opts);
 
 /* Create a solve on the current CUDA device.
- *   nz, nr >= 1; tau > 1/2 (BGK relaxation time, nu = (tau - 1/2)/3);
+ *   nz, nr >= 1 with nz * nr <= 2^27 nodes and 9 * pitch * nr < 2^31, pitch
+ *   being nz rounded up to a multiple of 32 (the kernels address a population
+ *   buffer with 32-bit offsets); tau > 1/2 (BGK relaxation time, nu = (tau - 1/2)/3);
  *   eos: required when opts->multiphase (else may be NULL); A: Kupershtokh
  *   mixing parameter (A = -0.152 recovers the vdW coexistence curve);
  *   opts: NULL for the defaults.
@@ -175,9 +190,10 @@ int lbm_axi_time_kernels(lbm_axi* h, long long n, double* ms);
  *         (z-strip, row) space (default); > 0 -- fixed chunks of that many rows
  *         of one z-strip per CTA.
  * The default is FUSED (nr >= 16) with rows_per_cta = 0; a solve with
- * h_eval = LBM_H_LINK_AVG is SPLIT only.  The paths agree to rounding.
- * Setting waits for the handle's stream; it returns LBM_ERR_INVALID_ARG for an
- * unknown path, rows_per_cta < 0, or FUSED when nr < 16 or with LBM_H_LINK_AVG. */
+ * h_eval = LBM_H_LINK_AVG or forcing = LBM_FORCING_GUO is SPLIT only.  The paths
+ * agree to rounding.  Setting waits for the handle's stream; it returns
+ * LBM_ERR_INVALID_ARG for an unknown path, rows_per_cta < 0, or FUSED when
+ * nr < 16, with LBM_H_LINK_AVG or with LBM_FORCING_GUO. */
 enum { LBM_PATH_FUSED = 1, LBM_PATH_SPLIT = 2 };
 typedef struct {
     int path;

@@ -7,7 +7,7 @@ binds it and adds the EOS helpers (critical point, Maxwell construction) and
 the paper's analytic results used as pins (analytic.py).
 """
 from .core import (  # noqa: F401
-    EOS_CS, EOS_VDW, H_LINK_AVG, H_LOCAL, KAPPA_LATTICE, KAPPA_MIXED, KAPPA_THERMO, Oracle, OracleError, Params, Q, TOP_FREESLIP,
+    EOS_CS, EOS_VDW, FORCING_EDM, FORCING_GUO, H_LINK_AVG, H_LOCAL, KAPPA_LATTICE, KAPPA_MIXED, KAPPA_THERMO, Oracle, OracleError, Params, Q, TOP_FREESLIP,
     TOP_NOSLIP, TOP_PERIODIC,
 )
 from . import analytic, core, eos  # noqa: F401

@@ -15,6 +15,7 @@ TOP_FREESLIP, TOP_NOSLIP, TOP_PERIODIC = 0, 1, 2
 EOS_VDW, EOS_CS = 0, 1
 KAPPA_THERMO, KAPPA_LATTICE, KAPPA_MIXED = 0, 1, 2
 H_LOCAL, H_LINK_AVG = 0, 1
+FORCING_EDM, FORCING_GUO = 0, 1
 ERR_UNPHYSICAL = -4
 
 
@@ -24,7 +25,7 @@ class _CParams(C.Structure):
         ("eos", C.c_int), ("T", C.c_double), ("a", C.c_double), ("b", C.c_double),
         ("R", C.c_double), ("lam", C.c_double), ("top", C.c_int), ("axis", C.c_int),
         ("multiphase", C.c_int), ("kappa", C.c_int), ("hr_sign", C.c_int), ("gz", C.c_double),
-        ("r0", C.c_double), ("h_eval", C.c_int),
+        ("r0", C.c_double), ("h_eval", C.c_int), ("forcing", C.c_int),
     ]
 
 
@@ -50,6 +51,7 @@ class Params:
     gz: float = 0.0
     r0: float = 0.0
     h_eval: int = H_LOCAL
+    forcing: int = FORCING_EDM
 
     def replace(self, **kw):
         return dataclasses.replace(self, **kw)
@@ -58,14 +60,15 @@ class Params:
         return _CParams(*[getattr(self, f.name) for f in dataclasses.fields(self)])
 
 
-_lib = None
+_libs = {}
 _D = C.POINTER(C.c_double)
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(_build.build())
+def lib(omp=False):
+    """The parity build of the oracle, or with omp=True the OpenMP timing build
+    of the same source (bitwise the same results, all host cores)."""
+    if omp not in _libs:
+        L = C.CDLL(_build.build(omp=omp))
         P = C.POINTER(_CParams)
         sig = {
             "orc_eos_p": (C.c_double, [P, C.c_double]),
@@ -78,6 +81,7 @@ def lib():
             "orc_force_axis": (None, [C.c_double] * 8 + [_D, _D]),
             "orc_source_H": (None, [C.c_double] * 8 + [C.c_int, _D, _D]),
             "orc_source_h": (None, [C.c_double] * 5 + [_D]),
+            "orc_guo_source": (None, [C.c_double] * 5 + [_D]),
             "orc_stream_dest": (None, [P, C.c_int, C.c_int, C.c_int] + [C.POINTER(C.c_int)] * 3),
             "orc_stream": (None, [P, _D, _D]),
             "orc_run": (C.c_int, [P, _D, C.c_long]),
@@ -88,13 +92,19 @@ def lib():
             "orc_mass_rweighted": (C.c_double, [P, _D]),
             "orc_ghost_width": (C.c_int, []),
             "orc_ext_index": (C.c_long, [P, C.c_int, C.c_int]),
+            "orc_threads": (C.c_int, [C.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
-        _lib = L
-    return _lib
+        _libs[omp] = L
+    return _libs[omp]
+
+
+def threads(n=0, omp=True):
+    """Set (n > 0) and return the thread count of the OpenMP build."""
+    return lib(omp).orc_threads(int(n))
 
 
 def _ptr(a):
@@ -143,6 +153,12 @@ def source_H(r, rho, mu, uz, ur, duz_dr, dur_dz, dur_dr, hr_sign):
 def source_h(r, rho, ur, Hz, Hr):
     out = np.zeros(Q)
     lib().orc_source_h(r, rho, ur, Hz, Hr, _ptr(out))
+    return out
+
+
+def guo_source(tau, uz, ur, Fz, Fr):
+    out = np.zeros(Q)
+    lib().orc_guo_source(tau, uz, ur, Fz, Fr, _ptr(out))
     return out
 
 
@@ -200,10 +216,12 @@ def force_kupershtokh(params, psi_ext):
 # ---------------------------------------------------------------- the solve --
 
 class Oracle:
-    """One solve on the CPU: pre-collision populations f[9, nr, nz]."""
+    """One solve on the CPU: pre-collision populations f[9, nr, nz].
+    omp=True steps with the OpenMP timing build (same results, all cores)."""
 
-    def __init__(self, params):
+    def __init__(self, params, omp=False):
         self.params = params
+        self.omp = omp
         self.f = np.zeros((Q, params.nr, params.nz))
 
     def init(self, rho, uz=None, ur=None, physical=False):
@@ -222,7 +240,7 @@ class Oracle:
         return self
 
     def step(self, n=1):
-        rc = lib().orc_run(C.byref(self.params.c()), _ptr(self.f), int(n))
+        rc = lib(self.omp).orc_run(C.byref(self.params.c()), _ptr(self.f), int(n))
         if rc != 0:
             raise OracleError("oracle step failed with code %d" % rc)
         return self

@@ -11,7 +11,10 @@
  *
  * It is deliberately plain: whole-field passes over arrays that carry ghost
  * layers, one pass per quantity, in the order in which the paper introduces
- * the quantities.  No blocking, no fusion.  Populations are stored
+ * the quantities.  No blocking, no fusion.  The passes carry OpenMP pragmas
+ * over rows (every row of a pass is independent) for the timing build that
+ * runs on all host cores; the parity build compiles without OpenMP, and the
+ * two give bitwise the same results.  Populations are stored
  * pre-collision, f[i][j][k] with k (z) contiguous, and streamed by pushing.
  *
  * Grid: nz x nr nodes (k, j); r_j = j + 1/2 (the axis lies midway between
@@ -37,6 +40,7 @@ enum { ORC_TOP_FREESLIP = 0, ORC_TOP_NOSLIP = 1, ORC_TOP_PERIODIC = 2 };
 enum { ORC_EOS_VDW = 0, ORC_EOS_CS = 1 };
 enum { ORC_KAPPA_THERMO = 0, ORC_KAPPA_LATTICE = 1, ORC_KAPPA_MIXED = 2 };
 enum { ORC_H_LOCAL = 0, ORC_H_LINK_AVG = 1 };
+enum { ORC_FORCING_EDM = 0, ORC_FORCING_GUO = 1 };
 enum { ORC_OK = 0, ORC_ERR_UNPHYSICAL = -4 };
 
 typedef struct {
@@ -56,6 +60,7 @@ typedef struct {
     double r0;      /* row j sits at r = r0 + j + 1/2; 0 for a lattice that starts at the
                        axis.  r0 > 0 describes a window cut out of a larger lattice (tests). */
     int h_eval;     /* where h_i of Eq. (lbm) is evaluated: ORC_H_LOCAL or ORC_H_LINK_AVG */
+    int forcing;    /* how F enters the collision: ORC_FORCING_EDM (Sec. II.C) or ORC_FORCING_GUO (Sec. II.A) */
 } orc_params;
 
 /* ------------------------------------------------------------------ EOS -- */
@@ -142,6 +147,7 @@ static int orc_map_row(const orc_params* P, int j, int sign_axis, int sign_top, 
  * z, mirrored (with the given parities) or periodic in r. */
 void orc_fill_ghosts(const orc_params* P, double* a, int sign_axis, int sign_top) {
     int nz = P->nz;
+    #pragma omp parallel for
     for (int j = -ORC_G; j < P->nr + ORC_G; j++) {
         int s = 1;
         int js = orc_map_row(P, j, sign_axis, sign_top, &s);
@@ -159,6 +165,7 @@ void orc_fill_ghosts(const orc_params* P, double* a, int sign_axis, int sign_top
  * d_alpha phi(x) = 1/36 sum_{i=1..8} (8 phi(x + c_i) - phi(x + 2 c_i)) c_{i,alpha}.
  * Evaluated at every interior node of an extended field. */
 void orc_grad(const orc_params* P, const double* a, double* dz, double* dr) {
+    #pragma omp parallel for
     for (int j = 0; j < P->nr; j++) {
         for (int k = 0; k < P->nz; k++) {
             double sz = 0.0, sr = 0.0;
@@ -180,6 +187,7 @@ void orc_grad(const orc_params* P, const double* a, double* dz, double* dr) {
 /* Kupershtokh single-neighbour force, Eq. (kupershtokhforcing) with dt = 1:
  * F = 18/3 [A sum_i w_i psi^2(x+c_i) c_i + (1-2A) psi(x) sum_i w_i psi(x+c_i) c_i]. */
 void orc_force_kupershtokh(const orc_params* P, const double* psi, double* fz, double* fr) {
+    #pragma omp parallel for
     for (int j = 0; j < P->nr; j++) {
         for (int k = 0; k < P->nz; k++) {
             double s2z = 0.0, s2r = 0.0, s1z = 0.0, s1r = 0.0;
@@ -281,6 +289,7 @@ void orc_stream_dest(const orc_params* P, int k, int j, int i, int* kd, int* jd,
 void orc_stream(const orc_params* P, const double* fpost, double* fnext) {
     long n = (long)P->nz * P->nr;
     for (int i = 0; i < ORC_Q; i++) {
+        #pragma omp parallel for
         for (int j = 0; j < P->nr; j++) {
             for (int k = 0; k < P->nz; k++) {
                 int kd, jd, id;
@@ -322,7 +331,9 @@ static int orc_work_alloc(const orc_params* P, orc_work* w) {
  * Returns ORC_ERR_UNPHYSICAL when rho <= 0, psi^2 < 0 or a value is not finite. */
 static int orc_fields(const orc_params* P, const double* f, orc_work* w) {
     long n = (long)P->nz * P->nr;
+    int bad = 0;
     /* Moments, Sec. II.A: rho = sum_i f_i, j = sum_i c_i f_i. */
+    #pragma omp parallel for reduction(|:bad)
     for (int j = 0; j < P->nr; j++) {
         for (int k = 0; k < P->nz; k++) {
             double rho = 0.0, jz = 0.0, jr = 0.0;
@@ -332,26 +343,35 @@ static int orc_fields(const orc_params* P, const double* f, orc_work* w) {
                 jz += orc_cz[i] * fi;
                 jr += orc_cr[i] * fi;
             }
-            if (!(rho > 0.0) || !isfinite(rho) || !isfinite(jz) || !isfinite(jr)) return ORC_ERR_UNPHYSICAL;
+            if (!(rho > 0.0) || !isfinite(rho) || !isfinite(jz) || !isfinite(jr)) {
+                bad = 1;
+                continue;
+            }
             long e = orc_ext(P, k, j);
             w->rho[e] = rho;
             w->jz[e] = jz;
             w->jr[e] = jr;
         }
     }
+    if (bad) return ORC_ERR_UNPHYSICAL;
     /* Pseudopotential psi = sqrt(rho/3 - P_k(rho)) = sqrt(-U), Sec. II.C. */
+    #pragma omp parallel for reduction(|:bad)
     for (int j = 0; j < P->nr; j++) {
         for (int k = 0; k < P->nz; k++) {
             long e = orc_ext(P, k, j);
             double psi = 0.0;
             if (P->multiphase) {
                 double arg = w->rho[e] / 3.0 - orc_eos_p(P, w->rho[e]);
-                if (!(arg >= 0.0) || !isfinite(arg)) return ORC_ERR_UNPHYSICAL;
+                if (!(arg >= 0.0) || !isfinite(arg)) {
+                    bad = 1;
+                    continue;
+                }
                 psi = sqrt(arg);
             }
             w->psi[e] = psi;
         }
     }
+    if (bad) return ORC_ERR_UNPHYSICAL;
     orc_fill_ghosts(P, w->psi, +1, +1);
 
     /* F = F_K + F_axis + rho g. */
@@ -369,6 +389,7 @@ static int orc_fields(const orc_params* P, const double* f, orc_work* w) {
         orc_grad(P, w->psir, scratch, w->psirr);
         orc_grad(P, w->psiz, w->Hr, w->psirz);
     }
+    #pragma omp parallel for reduction(|:bad)
     for (int j = 0; j < P->nr; j++) {
         double r = P->r0 + j + 0.5;
         for (int k = 0; k < P->nz; k++) {
@@ -390,9 +411,10 @@ static int orc_fields(const orc_params* P, const double* f, orc_work* w) {
             w->u0r[e] = w->jr[e] / rho;
             w->uz[e] = w->u0z[e] + fz / (2.0 * rho);
             w->ur[e] = w->u0r[e] + fr / (2.0 * rho);
-            if (!isfinite(w->uz[e]) || !isfinite(w->ur[e])) return ORC_ERR_UNPHYSICAL;
+            if (!isfinite(w->uz[e]) || !isfinite(w->ur[e])) bad = 1;
         }
     }
+    if (bad) return ORC_ERR_UNPHYSICAL;
     /* Velocity derivatives for H (same stencil, physical u; u_z even, u_r odd
      * across the axis; at a no-slip top both odd). */
     if (P->axis) {
@@ -401,6 +423,7 @@ static int orc_fields(const orc_params* P, const double* f, orc_work* w) {
         orc_grad(P, w->uz, w->Hz, w->duzdr);
         orc_grad(P, w->ur, w->durdz, w->durdr);
         double nu = (P->tau - 0.5) / 3.0;
+        #pragma omp parallel for
         for (int j = 0; j < P->nr; j++) {
             double r = P->r0 + j + 0.5;
             for (int k = 0; k < P->nz; k++) {
@@ -414,18 +437,46 @@ static int orc_fields(const orc_params* P, const double* f, orc_work* w) {
     return ORC_OK;
 }
 
-/* Collision with EDM forcing and the axisymmetric source, Eq. (lbm) with h_i:
- * f*_i = f_i + (f_i^eq(rho,u0) - f_i)/tau + [f_i^eq(rho,u0+F/rho) - f_i^eq(rho,u0)] + h_i. */
+/* Guo forcing term of Sec. II.A with dt = 1 and c_s^2 = 1/3:
+ * S_i = w_i (1 - 1/(2 tau)) [(c_i - u).F / c_s^2 + (c_i.u)(c_i.F) / c_s^4],
+ * u the fluid velocity u0 + F/(2 rho).  The second term is printed as
+ * (c_i - u).(c_i - F)/c_s^4, which is not a vector identity of Guo's scheme
+ * (it is neither linear in F nor of zero mass); it is read as the second-order
+ * Hermite term (c_i.u)(c_i.F)/c_s^4 of Guo et al., whose moments are
+ * sum S_i = 0 and sum c_i S_i = (1 - 1/(2 tau)) F. */
+void orc_guo_source(double tau, double uz, double ur, double Fz, double Fr, double* S) {
+    double pre = 1.0 - 1.0 / (2.0 * tau);
+    for (int i = 0; i < ORC_Q; i++) {
+        double cmu_F = (orc_cz[i] - uz) * Fz + (orc_cr[i] - ur) * Fr;
+        double cu = orc_cz[i] * uz + orc_cr[i] * ur;
+        double cF = orc_cz[i] * Fz + orc_cr[i] * Fr;
+        S[i] = orc_w[i] * pre * (3.0 * cmu_F + 9.0 * cu * cF);
+    }
+}
+
+/* Collision with the axisymmetric source, Eq. (lbm) with h_i, and either
+ * EDM forcing (Sec. II.C; the default):
+ *   f*_i = f_i + (f_i^eq(rho,u0) - f_i)/tau + [f_i^eq(rho,u0+F/rho) - f_i^eq(rho,u0)] + h_i,
+ * or Guo forcing (Sec. II.A), whose equilibrium takes the fluid velocity u:
+ *   f*_i = f_i + (f_i^eq(rho,u) - f_i)/tau + S_i + h_i. */
 static void orc_collide(const orc_params* P, const double* f, orc_work* w) {
     long n = (long)P->nz * P->nr;
+    #pragma omp parallel for
     for (int j = 0; j < P->nr; j++) {
         double r = P->r0 + j + 0.5;
         for (int k = 0; k < P->nz; k++) {
             long e = orc_ext(P, k, j);
             double rho = w->rho[e];
-            double feq0[ORC_Q], feq1[ORC_Q], h[ORC_Q];
-            orc_feq(rho, w->u0z[e], w->u0r[e], feq0);
-            orc_feq(rho, w->u0z[e] + w->Fz[e] / rho, w->u0r[e] + w->Fr[e] / rho, feq1);
+            double feq[ORC_Q], S[ORC_Q], h[ORC_Q];
+            if (P->forcing == ORC_FORCING_GUO) {
+                orc_feq(rho, w->uz[e], w->ur[e], feq);
+                orc_guo_source(P->tau, w->uz[e], w->ur[e], w->Fz[e], w->Fr[e], S);
+            } else {
+                double feq1[ORC_Q];
+                orc_feq(rho, w->u0z[e], w->u0r[e], feq);
+                orc_feq(rho, w->u0z[e] + w->Fz[e] / rho, w->u0r[e] + w->Fr[e] / rho, feq1);
+                for (int i = 0; i < ORC_Q; i++) S[i] = feq1[i] - feq[i];
+            }
             if (P->axis) {
                 orc_source_h(r, rho, w->ur[e], w->Hz[e], w->Hr[e], h);
                 if (P->h_eval == ORC_H_LINK_AVG)
@@ -435,7 +486,7 @@ static void orc_collide(const orc_params* P, const double* f, orc_work* w) {
             }
             for (int i = 0; i < ORC_Q; i++) {
                 long c = i * n + (long)j * P->nz + k;
-                w->fpost[c] = f[c] + (feq0[i] - f[c]) / P->tau + (feq1[i] - feq0[i]) + h[i];
+                w->fpost[c] = f[c] + (feq[i] - f[c]) / P->tau + S[i] + h[i];
             }
         }
     }
@@ -452,6 +503,7 @@ static void orc_collide(const orc_params* P, const double* f, orc_work* w) {
  * Called after streaming, with the fields of the step that just collided. */
 static void orc_arrival_half(const orc_params* P, const orc_work* w, double* f) {
     long n = (long)P->nz * P->nr;
+    #pragma omp parallel for
     for (int j = 0; j < P->nr; j++) {
         double r = P->r0 + j + 0.5;
         for (int k = 0; k < P->nz; k++) {
@@ -582,6 +634,21 @@ double orc_mass_rweighted(const orc_params* P, const double* f) {
         }
     }
     return m;
+}
+
+/* Threads the whole-field passes use: n > 0 sets the count of an OpenMP build
+ * (the plain build ignores it and runs on one thread); returns the count in use. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int orc_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* Test hooks for extended (ghosted) fields: size and index of node (k, j). */

@@ -113,13 +113,13 @@ cudaError_t enqueue_step(lbm_axi* h) {
         e = Ops<float>::density(h->pf, (const float*)h->f[c], (float*)h->aux, h->derr, h->stream, lk);
         if (e == cudaSuccess)
             e = Ops<float>::update(h->pf, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1], (const float*)h->aux,
-                                   h->stream, lk);
+                                   h->stream, lk, guo_of(h));
     } else {
         const lbm::LinkPlanes<double> lk = link_planes<double>(h, c);
         e = Ops<double>::density(h->pdd, (const double*)h->f[c], (double*)h->aux, h->derr, h->stream, lk);
         if (e == cudaSuccess)
             e = Ops<double>::update(h->pdd, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
-                                    (const double*)h->aux, h->stream, lk);
+                                    (const double*)h->aux, h->stream, lk, guo_of(h));
     }
     h->cur = c ^ 1;
     return e;
@@ -238,6 +238,7 @@ void lbm_axi_default_opts(lbm_axi_opts* o) {
     o->g_z = 0.0;
     o->stream = nullptr;
     o->h_eval = LBM_H_LOCAL;
+    o->forcing = LBM_FORCING_EDM;
 }
 
 size_t lbm_axi_footprint(int nz, int nr, int precision) {
@@ -255,11 +256,14 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     if (opts) o = *opts;
     else lbm_axi_default_opts(&o);
     if (nz < 1 || nr < 1 || (long long)nz * nr > (1LL << 31) / 16) return LBM_ERR_INVALID_ARG;
+    // the step kernels index a population buffer (9 planes of pitch x nr) with 32-bit offsets
+    if (9LL * pitch_of(nz) * nr >= (1LL << 31)) return LBM_ERR_INVALID_ARG;
     if (!(tau > 0.5) || !(tau < 1e6)) return LBM_ERR_INVALID_ARG;
     if (o.precision != 32 && o.precision != 64) return LBM_ERR_INVALID_ARG;
     if (o.top_bc < 0 || o.top_bc > 2 || o.kappa_mode < 0 || o.kappa_mode > 2) return LBM_ERR_INVALID_ARG;
     if (o.hr_sign != 1 && o.hr_sign != -1) return LBM_ERR_INVALID_ARG;
     if (o.h_eval != LBM_H_LOCAL && o.h_eval != LBM_H_LINK_AVG) return LBM_ERR_INVALID_ARG;
+    if (o.forcing != LBM_FORCING_EDM && o.forcing != LBM_FORCING_GUO) return LBM_ERR_INVALID_ARG;
     lbm_eos e;
     memset(&e, 0, sizeof(e));
     double T = 0.0, Tc = 0.0;
@@ -337,8 +341,8 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     }
     h->pf = make_params<float>(h);
     h->pdd = make_params<double>(h);
-    // the link-midpoint source is implemented on the two-kernel path only
-    h->path = nr >= lbm::kStepMinRows && !link ? LBM_PATH_FUSED : LBM_PATH_SPLIT;
+    // the link-midpoint source and Guo forcing are implemented on the two-kernel path only
+    h->path = nr >= lbm::kStepMinRows && !split_only(h) ? LBM_PATH_FUSED : LBM_PATH_SPLIT;
     h->rows_per_cta = 0;  // balanced single wave
     if (h->precision == 32) h->pdd = make_params_out(h);
     *h->herr = 0;
@@ -516,10 +520,10 @@ int lbm_axi_time_kernels(lbm_axi* h, long long n, double* ms) {
         } else if (e == cudaSuccess) {
             if (h->precision == 32)
                 e = Ops<float>::update(h->pf, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1],
-                                       (const float*)h->aux, h->stream, link_planes<float>(h, c));
+                                       (const float*)h->aux, h->stream, link_planes<float>(h, c), guo_of(h));
             else
                 e = Ops<double>::update(h->pdd, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
-                                        (const double*)h->aux, h->stream, link_planes<double>(h, c));
+                                        (const double*)h->aux, h->stream, link_planes<double>(h, c), guo_of(h));
         }
         if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(ev[2]);
@@ -566,16 +570,66 @@ int lbm_axi_moments(lbm_axi* h, double* rho, double* uz, double* ur, double* p) 
 
 // ------------------------------------------------------- checkpoint --
 // Blob: StateHeader, then the 9 population planes (nr x nz each, z fastest) in
-// the storage precision, exactly as the next step will read them.
+// the storage precision, exactly as the next step will read them.  The header
+// records the grid, precision, reference density and every parameter of the
+// dynamics, so that a blob only resumes a solve that continues the same run.
 namespace {
 struct StateHeader {
     char magic[8];  // "LBMAXIS1"
     int32_t version, precision, nz, nr;
     double rho_ref;
-    int32_t cur, reserved[7];
+    int32_t cur, link_planes, reserved[6];
+    // dynamics (format version 2)
+    double tau, A, T, T_over_Tc, a, b, R, lambda, g_z;
+    int32_t eos_kind, top_bc, axis_terms, multiphase, kappa_mode, hr_sign, h_eval, forcing;
+    double reserved2[3];
 };
-static_assert(sizeof(StateHeader) == 64, "checkpoint header layout");
+static_assert(sizeof(StateHeader) == 192, "checkpoint header layout");
 const char kStateMagic[8] = {'L', 'B', 'M', 'A', 'X', 'I', 'S', '1'};
+constexpr int32_t kStateVersion = 2;
+
+void fill_header(const lbm_axi* h, StateHeader* hd) {
+    memset(hd, 0, sizeof(*hd));
+    memcpy(hd->magic, kStateMagic, sizeof(kStateMagic));
+    hd->version = kStateVersion;
+    hd->precision = h->precision;
+    hd->nz = h->nz;
+    hd->nr = h->nr;
+    hd->rho_ref = stored_rho_ref(h);
+    hd->cur = h->cur;
+    hd->link_planes = h->hb[0] ? 1 : 0;
+    hd->tau = h->tau;
+    hd->A = h->A;
+    hd->T = h->T;
+    hd->T_over_Tc = h->opts.multiphase ? h->eos.T_over_Tc : 0.0;
+    hd->a = h->opts.multiphase ? h->eos.a : 0.0;
+    hd->b = h->opts.multiphase ? h->eos.b : 0.0;
+    hd->R = h->opts.multiphase ? h->eos.R : 0.0;
+    hd->lambda = h->opts.multiphase ? h->eos.lambda : 0.0;
+    hd->g_z = h->opts.g_z;
+    hd->eos_kind = h->opts.multiphase ? h->eos.kind : -1;
+    hd->top_bc = h->opts.top_bc;
+    hd->axis_terms = h->opts.axis_terms ? 1 : 0;
+    hd->multiphase = h->opts.multiphase ? 1 : 0;
+    hd->kappa_mode = h->opts.kappa_mode;
+    hd->hr_sign = h->opts.hr_sign;
+    hd->h_eval = h->opts.h_eval;
+    hd->forcing = h->opts.forcing;
+}
+
+// The blob continues this solve: same layout and the same dynamics, bit for bit.
+bool header_matches(const lbm_axi* h, const StateHeader& hd) {
+    StateHeader mine;
+    fill_header(h, &mine);
+    return memcmp(hd.magic, mine.magic, sizeof(mine.magic)) == 0 && hd.version == mine.version &&
+           hd.precision == mine.precision && hd.nz == mine.nz && hd.nr == mine.nr && hd.rho_ref == mine.rho_ref &&
+           (hd.cur == 0 || hd.cur == 1) && hd.link_planes == mine.link_planes && hd.tau == mine.tau &&
+           hd.A == mine.A && hd.T == mine.T && hd.T_over_Tc == mine.T_over_Tc && hd.a == mine.a &&
+           hd.b == mine.b && hd.R == mine.R && hd.lambda == mine.lambda && hd.g_z == mine.g_z &&
+           hd.eos_kind == mine.eos_kind && hd.top_bc == mine.top_bc && hd.axis_terms == mine.axis_terms &&
+           hd.multiphase == mine.multiphase && hd.kappa_mode == mine.kappa_mode && hd.hr_sign == mine.hr_sign &&
+           hd.h_eval == mine.h_eval && hd.forcing == mine.forcing;
+}
 
 // planes in the blob: the 9 populations, then (link-midpoint source) the 3 source planes
 int state_planes(const lbm_axi* h) { return h->hb[0] ? 12 : 9; }
@@ -595,15 +649,7 @@ int lbm_axi_save(lbm_axi* h, void* buf, size_t bytes) {
     if (!h->initialized) return LBM_ERR_STATE;
     DeviceGuard g(h->device);
     StateHeader hd;
-    memset(&hd, 0, sizeof(hd));
-    memcpy(hd.magic, kStateMagic, sizeof(kStateMagic));
-    hd.version = 1;
-    hd.precision = h->precision;
-    hd.nz = h->nz;
-    hd.nr = h->nr;
-    hd.rho_ref = stored_rho_ref(h);
-    hd.cur = h->cur;
-    hd.reserved[0] = h->hb[0] ? 1 : 0;
+    fill_header(h, &hd);
     memcpy(buf, &hd, sizeof(hd));
     const size_t es = h->precision == 32 ? 4 : 8;
     char* dst = static_cast<char*>(buf) + sizeof(hd);
@@ -624,10 +670,7 @@ int lbm_axi_load(lbm_axi* h, const void* buf, size_t bytes) {
     if (!h || !buf || bytes < sizeof(StateHeader)) return LBM_ERR_INVALID_ARG;
     StateHeader hd;
     memcpy(&hd, buf, sizeof(hd));
-    if (memcmp(hd.magic, kStateMagic, sizeof(kStateMagic)) != 0 || hd.version != 1 ||
-        hd.precision != h->precision || hd.nz != h->nz || hd.nr != h->nr || hd.rho_ref != stored_rho_ref(h) ||
-        (hd.cur != 0 && hd.cur != 1) || hd.reserved[0] != (h->hb[0] ? 1 : 0) || bytes < state_bytes(h))
-        return LBM_ERR_INVALID_ARG;
+    if (!header_matches(h, hd) || bytes < state_bytes(h)) return LBM_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     const size_t es = h->precision == 32 ? 4 : 8;
     const char* src = static_cast<const char*>(buf) + sizeof(hd);
@@ -708,7 +751,7 @@ int lbm_axi_get_tuning(const lbm_axi* h, lbm_axi_tuning* t) {
 int lbm_axi_set_tuning(lbm_axi* h, const lbm_axi_tuning* t) {
     if (!h || !t) return LBM_ERR_INVALID_ARG;
     if (t->path != LBM_PATH_FUSED && t->path != LBM_PATH_SPLIT) return LBM_ERR_INVALID_ARG;
-    if (t->path == LBM_PATH_FUSED && (h->nr < lbm::kStepMinRows || h->hb[0])) return LBM_ERR_INVALID_ARG;
+    if (t->path == LBM_PATH_FUSED && (h->nr < lbm::kStepMinRows || split_only(h))) return LBM_ERR_INVALID_ARG;
     if (t->rows_per_cta < 0 || t->rows_per_cta > (1 << 20)) return LBM_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ERR_CUDA;

@@ -163,7 +163,7 @@ int lbm_axi_batch_create(lbm_axi* const* solves, int n, void* stream, lbm_axi_ba
         const lbm_axi* h = solves[i];
         if (!h || !h->initialized || h->device != dev || h->precision != h0->precision ||
             h->nr < lbm::kStepMinRows || h->opts.multiphase != h0->opts.multiphase ||
-            h->opts.axis_terms != h0->opts.axis_terms || h->hb[0])  // (no link-midpoint source in the batch)
+            h->opts.axis_terms != h0->opts.axis_terms || split_only(h))  // (two-kernel-only options)
             return LBM_ERR_INVALID_ARG;
         for (int k = 0; k < i; k++)
             if (solves[k] == h) return LBM_ERR_INVALID_ARG;
@@ -389,17 +389,17 @@ int lbm_axi_autotune(lbm_axi* h, int trials, lbm_axi_tuning* chosen) {
             e = Ops<float>::density(h->pf, (const float*)h->f[c], (float*)h->aux, h->derr, h->stream, lk);
             if (e == cudaSuccess)
                 e = Ops<float>::update(h->pf, h->pdd, (const float*)h->f[c], (float*)h->f[c ^ 1],
-                                       (const float*)h->aux, h->stream, lk);
+                                       (const float*)h->aux, h->stream, lk, guo_of(h));
         } else {
             const lbm::LinkPlanes<double> lk = link_planes<double>(h, c);
             e = Ops<double>::density(h->pdd, (const double*)h->f[c], (double*)h->aux, h->derr, h->stream, lk);
             if (e == cudaSuccess)
                 e = Ops<double>::update(h->pdd, h->pdd, (const double*)h->f[c], (double*)h->f[c ^ 1],
-                                        (const double*)h->aux, h->stream, lk);
+                                        (const double*)h->aux, h->stream, lk, guo_of(h));
         }
         return e;
     };
-    if (h->nr >= lbm::kStepMinRows && !h->hb[0]) {  // the fused forms lack the link-midpoint source
+    if (h->nr >= lbm::kStepMinRows && !split_only(h)) {  // the fused forms lack these options
         const int rows_list[5] = {0, 32, 64, 144, 256};
         for (int q = 0; q < 5; q++) {
             const float ms = time_launches(h->stream, trials, [&] { return fused(rows_list[q]); });

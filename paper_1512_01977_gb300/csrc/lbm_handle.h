@@ -53,6 +53,11 @@ inline lbm::LinkPlanes<R> link_planes(const lbm_axi* h, int c) {
     return {static_cast<const R*>(h->hb[c]), static_cast<R*>(h->hb[c ^ 1])};
 }
 
+// Guo forcing in place of the EDM shift (two-kernel path only).
+inline bool guo_of(const lbm_axi* h) { return h->opts.forcing == LBM_FORCING_GUO; }
+// Options that only the two-kernel path implements (no fused step, no batch).
+inline bool split_only(const lbm_axi* h) { return h->hb[0] != nullptr || guo_of(h); }
+
 // Step parity bookkeeping used by the batch API: after n steps run outside
 // the handle's own step loop, its current buffer flips when n is odd.
 inline void lbm_handle_advance(lbm_axi* h, long long n) {

@@ -112,10 +112,11 @@ struct TileShape {
     static constexpr int elems = PW * PH + 2 * DW * DH + 5 * UW * UH + 2 * TZ * TR;
 };
 
+// guo != 0: Guo forcing (Sec. II.A) in place of the EDM shift (only this kernel has it).
 template <typename R, int TZ, int TR, bool MOMENTS>
 __global__ void __launch_bounds__(256) k_update(Params<R> p, Params<double> pd, const R* __restrict__ f,
                                                 R* __restrict__ fout, const R* __restrict__ aux,
-                                                double* __restrict__ mout, LinkPlanes<R> lk) {
+                                                double* __restrict__ mout, LinkPlanes<R> lk, int guo) {
     using S = TileShape<TZ, TR>;
     constexpr int PW = S::PW, PH = S::PH, DW = S::DW, DH = S::DH, UW = S::UW, UH = S::UH;
     constexpr int NT = 256;
@@ -258,6 +259,11 @@ __global__ void __launch_bounds__(256) k_update(Params<R> p, Params<double> pd, 
         const R u0sq = u0z * u0z + u0r * u0r;
         const R sz = R(2) * u0z + duz, sr = R(2) * u0r + dur;  // u0 + u1
         const R dusum = duz * sz + dur * sr;                   // u1^2 - u0^2
+        // Guo forcing: f^eq at the fluid velocity u, and
+        // S_i = w_i (1 - 1/(2 tau)) [3 (c_i - u).F + 9 (c_i.u)(c_i.F)]
+        const R Fz = sFz[ti * TZ + tk], Fr = sFr[ti * TZ + tk];
+        const R usq = uz * uz + ur * ur, uF = uz * Fz + ur * Fr;
+        const R gpre = R(1) - R(0.5) * p.tau_inv;
         const long long o = (long long)j * p.pitch + k;
         // link-midpoint source: arrival half of the previous step's h at this
         // node, departure half of this step's; this step's S0, H kept for the next
@@ -277,15 +283,22 @@ __global__ void __launch_bounds__(256) k_update(Params<R> p, Params<double> pd, 
             const R cx = R(cz_of(i)), cy = R(cr_of(i));
             R fi = f[pull_slot(p, k, j, i)];
             if (lk.src) fi += R(0.5) * w * (a0 + R(3) * (cx * az + cy * ar));
-            const R cu0 = cx * u0z + cy * u0r;
-            const R cdu = cx * duz + cy * dur;
-            const R csum = cx * sz + cy * sr;
-            // f^eq(rho, u0) - w_i rho_ref (Sec. II.A), the EDM shift
-            // f^eq(rho, u0 + F/rho) - f^eq(rho, u0) written as a difference, and h_i (Sec. II.B).
-            const R feq = w * (drho + rho * (R(3) * cu0 + R(4.5) * cu0 * cu0 - R(1.5) * u0sq));
-            const R edm = w * rho * (R(3) * cdu + R(4.5) * cdu * csum - R(1.5) * dusum);
-            const R h = hs * w * (m0 + R(3) * (cx * Hz + cy * Hr));
-            fout[i * p.plane + o] = fi + (feq - fi) * p.tau_inv + edm + h;
+            R feq, force;
+            if (guo) {
+                const R cu = cx * uz + cy * ur, cF = cx * Fz + cy * Fr;
+                feq = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq));
+                force = w * gpre * (R(3) * (cF - uF) + R(9) * cu * cF);
+            } else {
+                const R cu0 = cx * u0z + cy * u0r;
+                const R cdu = cx * duz + cy * dur;
+                const R csum = cx * sz + cy * sr;
+                // f^eq(rho, u0) - w_i rho_ref (Sec. II.A) and the EDM shift
+                // f^eq(rho, u0 + F/rho) - f^eq(rho, u0) written as a difference
+                feq = w * (drho + rho * (R(3) * cu0 + R(4.5) * cu0 * cu0 - R(1.5) * u0sq));
+                force = w * rho * (R(3) * cdu + R(4.5) * cdu * csum - R(1.5) * dusum);
+            }
+            const R h = hs * w * (m0 + R(3) * (cx * Hz + cy * Hr));  // h_i (Sec. II.B)
+            fout[i * p.plane + o] = fi + (feq - fi) * p.tau_inv + force + h;
         }
     }
 }
@@ -380,18 +393,30 @@ __global__ void __launch_bounds__(256) k_pjump(Params<R> p, Params<double> pd, c
     block_sum<4>(v, partial + 4 * blockIdx.x);
 }
 
+// Final sum of the per-block partials by one warp (launch <<<1, 32>>>): lane l
+// adds partials l, l + 32, l + 64, ... in that order, then a shuffle tree
+// combines the lanes.  The order is fixed, so the result is bitwise
+// reproducible for a given number of partials.
 template <int N>
 __global__ void k_reduce_final(const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     double s[N];
 #pragma unroll
     for (int q = 0; q < N; q++) s[q] = 0.0;
-    for (int b = 0; b < nblocks; b++) {
+    for (int b = lane; b < nblocks; b += 32) {
 #pragma unroll
         for (int q = 0; q < N; q++) s[q] += partial[N * b + q];
     }
 #pragma unroll
-    for (int q = 0; q < N; q++) out[q] = s[q];
+    for (int q = 0; q < N; q++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[q] += __shfl_down_sync(0xffffffffu, s[q], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < N; q++) out[q] = s[q];
+    }
 }
 
 }  // namespace lbm

@@ -20,9 +20,10 @@ struct Ops {
     // lk: the link-midpoint source planes (null: h_i at the node).
     static cudaError_t density(const Params<R>& p, const R* f, R* aux, int* err, cudaStream_t s,
                                LinkPlanes<R> lk = {nullptr, nullptr});
-    // kernel (b): the fused stream + force + EDM + axisymmetric source + collide step.
+    // kernel (b): the fused stream + force + EDM + axisymmetric source + collide step
+    // (guo: Guo forcing in place of the EDM shift).
     static cudaError_t update(const Params<R>& p, const Params<double>& pd, const R* f, R* fout, const R* aux,
-                              cudaStream_t s, LinkPlanes<R> lk = {nullptr, nullptr});
+                              cudaStream_t s, LinkPlanes<R> lk = {nullptr, nullptr}, bool guo = false);
     // rho, physical u, P_k of the current state into mout[4][nz*nr] (after density()).
     static cudaError_t moments(const Params<R>& p, const Params<double>& pd, const R* f, const R* aux,
                                double* mout, cudaStream_t s);
@@ -44,7 +45,7 @@ struct Ops {
     static size_t step_smem();
     static int step_strip();  // z-columns per CTA of the single-pass kernel
     // Batched fused step over nsolves solves (device arrays solves[n], start[n+1]).
-    // strip: 64 or 128 z-columns per CTA; grid: CTAs (0 = one resident wave).
+    // strip: kStripNarrow or kStripWide z-columns per CTA; grid: CTAs (0 = one resident wave).
     static cudaError_t step_batch(const BatchSolve<R>* solves, const long long* start, int nsolves, bool mp,
                                   bool ax, int parity, int strip, int grid, int* err, cudaStream_t s);
     static int batch_resident_ctas(int strip);

@@ -27,14 +27,14 @@ size_t Ops<R>::update_smem() {
 
 template <typename R>
 static cudaError_t launch_update(const Params<R>& p, const Params<double>& pd, const R* f, R* fout, const R* aux,
-                                 double* mout, bool moments, cudaStream_t s, LinkPlanes<R> lk) {
+                                 double* mout, bool moments, cudaStream_t s, LinkPlanes<R> lk, bool guo) {
     using T = UpdateTile<R>;
     const size_t smem = Ops<R>::update_smem();
     dim3 grid((p.nz + T::TZ - 1) / T::TZ, (p.nr + T::TR - 1) / T::TR);
     if (moments) {
-        k_update<R, T::TZ, T::TR, true><<<grid, 256, smem, s>>>(p, pd, f, nullptr, aux, mout, lk);
+        k_update<R, T::TZ, T::TR, true><<<grid, 256, smem, s>>>(p, pd, f, nullptr, aux, mout, lk, 0);
     } else {
-        k_update<R, T::TZ, T::TR, false><<<grid, 256, smem, s>>>(p, pd, f, fout, aux, nullptr, lk);
+        k_update<R, T::TZ, T::TR, false><<<grid, 256, smem, s>>>(p, pd, f, fout, aux, nullptr, lk, guo ? 1 : 0);
     }
     return cudaGetLastError();
 }
@@ -150,14 +150,14 @@ cudaError_t Ops<R>::density(const Params<R>& p, const R* f, R* aux, int* err, cu
 
 template <typename R>
 cudaError_t Ops<R>::update(const Params<R>& p, const Params<double>& pd, const R* f, R* fout, const R* aux,
-                           cudaStream_t s, LinkPlanes<R> lk) {
-    return launch_update<R>(p, pd, f, fout, aux, nullptr, false, s, lk);
+                           cudaStream_t s, LinkPlanes<R> lk, bool guo) {
+    return launch_update<R>(p, pd, f, fout, aux, nullptr, false, s, lk, guo);
 }
 
 template <typename R>
 cudaError_t Ops<R>::moments(const Params<R>& p, const Params<double>& pd, const R* f, const R* aux, double* mout,
                             cudaStream_t s) {
-    return launch_update<R>(p, pd, f, nullptr, aux, mout, true, s, LinkPlanes<R>{nullptr, nullptr});
+    return launch_update<R>(p, pd, f, nullptr, aux, mout, true, s, LinkPlanes<R>{nullptr, nullptr}, false);
 }
 
 template <typename R>

@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 from paper_1512_01977_gb300 import inputs as I
-from tests._cases import Case, rel_err, run_oracle, vel_err
+from tests._cases import Case, component_errs, rel_err, run_oracle, vel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -70,17 +70,32 @@ def test_batch_equals_alone(lbm, precision, strip):
         s.close()
 
 
-def test_batch_fp64_matches_oracle(lbm):
+@pytest.mark.parametrize("strip", [64, 96])
+def test_batch_fp64_matches_oracle(lbm, strip):
+    """An FP64 batch whose mix holds grids wider than one strip (up to 230
+    columns: several strips and a ragged last one) against the oracle."""
     mix = _mix(seed=11, n=4)
+    for nz, nr in ((230, 30), (131, 41)):
+        c = Case(nz, nr, tau=1.0, T_over_Tc=0.85)
+        rv, rl = c.coexistence()
+        rho, _, _ = I.droplet(nz, nr, 10, rl, rv)
+        rho = np.maximum(rho, np.roll(rho, nz // 2, axis=1))
+        _, vz, vr = I.random_state(nz, nr, 1.0, 0.0, 1e-3, nz)
+        mix.append((c, (rho, vz, vr * (np.arange(nr) + 0.5)[:, None] / nr), 0.0))
     solvers = [c.solver().init(*fields) for c, fields, _ in mix]
     b = lbm.Batch(solvers)
+    lbm.lbm_axi_batch_set_tuning(b.b, strip, 0)
     b.step(60)
     for (c, fields, _), s in zip(mix, solvers):
         mo = run_oracle(c, fields, 60).moments()
         mg = s.moments()
         assert rel_err(mg["rho"], mo["rho"]) <= 1e-12
         assert vel_err(mg, mo) <= 1e-12
+        for k, e in component_errs(mg, mo).items():
+            assert e is None or e <= 1e-12, (c.nz, c.nr, k, e)
     b.close()
+    for s in solvers:
+        s.close()
 
 
 def test_failed_solve_is_isolated(lbm):

@@ -73,3 +73,13 @@ def test_host_eos_matches_oracle(lbm, kind, T):
 def test_invalid_eos_rejected(lbm):
     with pytest.raises(lbm.LbmError):
         lbm.lbm_eos_coexistence(lbm.make_eos(O.EOS_CS, 1.2))
+
+
+@pytest.mark.parametrize("nz,nr", [(16, 8388608), (1, 1 << 27), (4096, 1 << 16)])
+def test_create_refuses_grids_beyond_32bit_offsets(lbm, nz, nr):
+    """Grids whose population buffer (9 planes of pitch x nr, pitch = nz
+    rounded up to 32) reaches 2^31 elements, or that exceed 2^27 nodes, are
+    refused before any device call."""
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_axi_create(nz, nr, 1.0, lbm.make_eos(), -0.152)
+    assert e.value.code == lbm.ERR_INVALID_ARG

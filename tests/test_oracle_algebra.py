@@ -322,3 +322,74 @@ def test_stream_is_a_permutation_with_the_boundary_rules(top, nz, nr):
                 else:
                     assert (kd, jd, CZ[idd], CR[idd]) == (k, j, -CZ[i], -CR[i])
     assert len(seen) == 9 * nz * nr
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_guo_source_moments(seed):
+    """Guo forcing (Sec. II.A, second term read as (c_i.u)(c_i.F)/c_s^4): the
+    source adds no mass, momentum (1 - 1/(2 tau)) F and second moment
+    (1 - 1/(2 tau)) (u F + F u).  The printed (c_i - u).(c_i - F) term would
+    put mass into the source and break the first of these."""
+    rng = np.random.default_rng(seed)
+    _, cz, cr = _lattice_from_feq()
+    tau = rng.uniform(0.55, 2.0)
+    uz, ur, Fz, Fr = rng.uniform(-0.1, 0.1, size=4)
+    S = core.guo_source(tau, uz, ur, Fz, Fr)
+    pre = 1 - 1 / (2 * tau)
+    assert abs(S.sum()) < 1e-16
+    assert (S * cz).sum() == pytest.approx(pre * Fz, rel=1e-13)
+    assert (S * cr).sum() == pytest.approx(pre * Fr, rel=1e-13)
+    assert (S * cz * cz).sum() == pytest.approx(pre * 2 * uz * Fz, rel=1e-12, abs=1e-17)
+    assert (S * cr * cr).sum() == pytest.approx(pre * 2 * ur * Fr, rel=1e-12, abs=1e-17)
+    assert (S * cz * cr).sum() == pytest.approx(pre * (uz * Fr + ur * Fz), rel=1e-12, abs=1e-17)
+
+
+def _collision_moments(forcing, seed):
+    """One collision of a multiphase state (plane mode, no h_i): per node the
+    moments of f* - f, the pre-collision moments and the force F."""
+    from paper_1512_01977_gb300 import inputs as I
+
+    p = O.make_params(24, 20, 0.8, O.EOS_CS, 0.85, top=O.TOP_PERIODIC, axis=0, forcing=forcing)
+    rv, rl = O.eos.maxwell_densities(p)
+    rho, uz, ur = I.droplet_2d(24, 20, 6, rl, rv)
+    _, vz, vr = I.random_state(24, 20, 1.0, 0.0, 2e-3, seed)
+    o = O.Oracle(p).init(rho, vz, vr)
+    d = o.moments(diagnostics=True)
+    post = o.collide_only()
+    _, cz, cr = _lattice_from_feq()
+    c = [np.ones(9), cz, cr]
+    dm = [[np.tensordot(a * b, post - o.f, axes=(0, 0)) for b in c] for a in c]
+    m = [[np.tensordot(a * b, o.f, axes=(0, 0)) for b in c] for a in c]
+    return p, d, dm, m
+
+
+@pytest.mark.parametrize("forcing", [O.FORCING_EDM, O.FORCING_GUO])
+def test_collision_moments_with_force(forcing):
+    """Per node, one collision with either forcing keeps the mass and adds F
+    to the momentum (both schemes give the fluid velocity u = u0 + F/(2 rho)).
+    Second moment: EDM, Pi* = Pi + (Pi_eq(u0) - Pi)/tau + rho (u1 u1 - u0 u0),
+    u1 = u0 + F/rho (the equilibrium shift of Sec. II.C); Guo,
+    Pi* = Pi + (Pi_eq(u) - Pi)/tau + (1 - 1/(2 tau)) (u F + F u)."""
+    p, d, dm, m = _collision_moments(forcing, 3)
+    rho, jz, jr = m[0][0], m[0][1], m[0][2]
+    Fz, Fr = d["Fz"], d["Fr"]
+    assert np.max(np.abs(Fz)) > 1e-4  # the interface carries a real force
+    assert np.max(np.abs(dm[0][0])) < 1e-15
+    np.testing.assert_allclose(dm[0][1], Fz, rtol=1e-11, atol=1e-15)
+    np.testing.assert_allclose(dm[0][2], Fr, rtol=1e-11, atol=1e-15)
+    tau = p.tau
+    if forcing == O.FORCING_EDM:
+        vz, vr = jz / rho, jr / rho
+        wz, wr = vz + Fz / rho, vr + Fr / rho
+        extra = lambda a, b: rho * (a[1] * b[1] - a[0] * b[0])  # noqa: E731
+        shift = {(1, 1): extra((vz, wz), (vz, wz)), (2, 2): extra((vr, wr), (vr, wr)),
+                 (1, 2): extra((vz, wz), (vr, wr))}
+    else:
+        vz, vr = (jz + Fz / 2) / rho, (jr + Fr / 2) / rho
+        pre = 1 - 1 / (2 * tau)
+        shift = {(1, 1): pre * 2 * vz * Fz, (2, 2): pre * 2 * vr * Fr, (1, 2): pre * (vz * Fr + vr * Fz)}
+    ueq = {1: vz, 2: vr}
+    for (a, b), s in shift.items():
+        pi_eq = rho * ueq[a] * ueq[b] + (rho / 3 if a == b else 0.0)
+        expect = (pi_eq - m[a][b]) / tau + s
+        np.testing.assert_allclose(dm[a][b], expect, rtol=1e-9, atol=1e-14)
