@@ -3,8 +3,8 @@
  *
  * Many independent solves (e.g. droplets of different sizes, temperatures and
  * relaxation times) advance together: each batch step is ONE launch of the
- * fused step kernel over a concatenation of all solves' (z-strip, row)
- * spaces, cut into equal shares for a one-wave grid; steps are replayed from
+ * fused step kernel over a work list of tiles -- row ranges of the solves'
+ * z-strips -- dealt to the CTAs by lbm_axi_tile_plan; steps are replayed from
  * a CUDA graph.  The update of every solve is exactly the single-solve update
  * (Sec. II of arXiv:1512.01977); no arithmetic couples two solves, so a
  * solve's result is the same alone and in any batch.
@@ -20,8 +20,8 @@ extern "C" {
 
 typedef struct lbm_axi_batch lbm_axi_batch;
 
-/* strip: z-columns per CTA, 64 or 96; grid: CTAs per launch, 0 = one wave of
- * resident CTAs. */
+/* strip: z-columns per CTA, 64 or 96; grid: CTA slots the tiles are dealt to,
+ * 0 = one wave of resident CTAs. */
 typedef struct {
     int strip;
     int grid;
@@ -58,7 +58,7 @@ int lbm_axi_batch_get_tuning(const lbm_axi_batch* b, lbm_axi_batch_tuning* t);
 int lbm_axi_batch_set_tuning(lbm_axi_batch* b, const lbm_axi_batch_tuning* t);
 
 /* Autotuner: time `trials` launches of every candidate configuration (strip
- * 64 / 96 x grid of one or two resident waves) on this batch, keep the
+ * 64 / 96 x tiles dealt to one or two resident waves) on this batch, keep the
  * fastest and return it in *chosen (may be NULL).  Non-destructive: trial
  * launches read the current populations and write only the buffer the next
  * step overwrites; error words raised by trials are cleared.  Synchronous. */
@@ -69,6 +69,28 @@ int lbm_axi_batch_autotune(lbm_axi_batch* b, int trials, lbm_axi_batch_tuning* c
  * (set as the solve's tuning) and returns it in *chosen (may be NULL).
  * Non-destructive like lbm_axi_batch_autotune.  Synchronous. */
 int lbm_axi_autotune(lbm_axi* h, int trials, lbm_axi_tuning* chosen);
+
+/* Work plan of a batched launch (performance only; no counterpart in the
+ * paper).  Every solve's (z-strip, row) space -- strip columns per strip,
+ * ceil(nz[i] / strip) strips -- is cut into tiles, rows [j0, jend) of one strip
+ * of one solve, and the tiles are dealt to `slots` CTAs, largest first, each to
+ * the CTA with the least work so far; a CTA marches its tiles one after
+ * another.  A tile costs its rows plus 18 rows of pipeline fill (6 halo rows
+ * above it and the 12-row lag between the kernel's first and last stage); of
+ * the candidate cuts (whole strips, or the smallest chunk height of at least
+ * 16 rows that fills 1..4 waves of slots) the one with the smallest largest
+ * CTA cost is kept.  A single solve is planned the same way (wide strips, one
+ * wave).  Host-only, no GPU.
+ *   nz, nr: n >= 1 grid sizes (host arrays); strip >= 1; slots >= 1;
+ *   tiles_out: 4 ints per tile (solve, strip, j0, jend), grouped by CTA,
+ *   max_tiles of room; first_out: the tiles of CTA c are first_out[c] ..
+ *   first_out[c + 1] - 1 (room for slots + 1 ints); *ntiles: tiles; *ncta: CTAs
+ *   with work (first_out[*ncta] = *ntiles); *makespan (may be NULL): the
+ *   largest CTA cost in rows.
+ * Returns LBM_ERR_INVALID_ARG for bad sizes, NULL outputs, or max_tiles too
+ * small (then *ntiles and *ncta still hold the counts needed). */
+int lbm_axi_tile_plan(const int* nz, const int* nr, int n, int strip, int slots, int max_tiles, int* tiles_out,
+                      int* first_out, int* ntiles, int* ncta, long long* makespan);
 
 /* Release the batch (waits for its stream).  The solves remain valid and keep
  * the state the batch left them in. */

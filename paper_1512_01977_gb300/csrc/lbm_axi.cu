@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "lbm_axi.h"
 #include "lbm_eos_host.h"
@@ -90,11 +91,11 @@ cudaError_t enqueue_step(lbm_axi* h) {
         // solve runs the same code alone as inside any batch
         const bool mp = h->opts.multiphase != 0, ax = h->opts.axis_terms != 0;
         if (h->precision == 32)
-            e = Ops<float>::step_batch(static_cast<const lbm::BatchSolve<float>*>(h->d_self), h->d_self_start, 1,
-                                       mp, ax, c, lbm::kStripWide, 0, h->derr, h->stream);
+            e = Ops<float>::step_batch(static_cast<const lbm::BatchSolve<float>*>(h->d_self), h->d_tiles,
+                                       h->d_first, h->ncta, mp, ax, c, lbm::kStripWide, h->derr, h->stream);
         else
-            e = Ops<double>::step_batch(static_cast<const lbm::BatchSolve<double>*>(h->d_self), h->d_self_start,
-                                        1, mp, ax, c, lbm::kStripWide, 0, h->derr, h->stream);
+            e = Ops<double>::step_batch(static_cast<const lbm::BatchSolve<double>*>(h->d_self), h->d_tiles,
+                                        h->d_first, h->ncta, mp, ax, c, lbm::kStripWide, h->derr, h->stream);
         h->cur = c ^ 1;
         return e;
     }
@@ -213,7 +214,8 @@ void release_all(lbm_axi* h) {
     dev_free(h->dred, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->derr, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->d_self, h->via_hook, h->hook_ctx, h->hook_release);
-    dev_free(h->d_self_start, h->via_hook, h->hook_ctx, h->hook_release);
+    dev_free(h->d_tiles, h->via_hook, h->hook_ctx, h->hook_release);
+    dev_free(h->d_first, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->hb[0], h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->hb[1], h->via_hook, h->hook_ctx, h->hook_release);
     if (h->herr) cudaFreeHost(h->herr);
@@ -310,7 +312,28 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     h->dred = (double*)dev_alloc(4 * sizeof(double));
     h->derr = (int*)dev_alloc(sizeof(int));
     h->d_self = dev_alloc(o.precision == 32 ? sizeof(lbm::BatchSolve<float>) : sizeof(lbm::BatchSolve<double>));
-    h->d_self_start = (long long*)dev_alloc(2 * sizeof(long long));
+    // tile plan of the balanced one-wave step (the batched kernel with a batch of one)
+    std::vector<lbm::Tile> tiles;
+    std::vector<int> first;
+    {
+        const int slots = o.precision == 32 ? Ops<float>::batch_resident_ctas(lbm::kStripWide)
+                                            : Ops<double>::batch_resident_ctas(lbm::kStripWide);
+        int rc = LBM_ERR_CUDA;
+        try {
+            rc = slots > 0 ? lbm::plan_tiles(&nz, &nr, 1, lbm::kStripWide, slots, tiles, first, nullptr)
+                           : LBM_ERR_CUDA;
+        } catch (...) {
+            rc = LBM_ERR_OOM;
+        }
+        if (rc != LBM_OK) {
+            release_all(h);
+            delete h;
+            return rc;
+        }
+    }
+    h->ncta = (int)first.size() - 1;
+    h->d_tiles = (lbm::Tile*)dev_alloc(tiles.size() * sizeof(lbm::Tile));
+    h->d_first = (int*)dev_alloc(first.size() * sizeof(int));
     h->bytes = lbm_axi_footprint(nz, nr, o.precision);
     const bool link = o.h_eval == LBM_H_LINK_AVG && o.axis_terms;
     if (link) {
@@ -319,7 +342,7 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
         h->bytes += 6 * plane_bytes;
     }
     bool ok = h->f[0] && h->f[1] && h->aux && h->mout && h->partial && h->dred && h->derr && h->d_self &&
-              h->d_self_start && (!link || (h->hb[0] && h->hb[1]));
+              h->d_tiles && h->d_first && (!link || (h->hb[0] && h->hb[1]));
     ok = ok && cudaMallocHost(&h->herr, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost(&h->hred, 4 * sizeof(double)) == cudaSuccess;
     if (!ok) {
@@ -348,8 +371,7 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     *h->herr = 0;
     cudaError_t err = cudaSuccess;
     {
-        // descriptor of this solve for the batched kernel (wide strips)
-        const long long start[2] = {0, (long long)((nz + lbm::kStripWide - 1) / lbm::kStripWide) * nr};
+        // descriptor of this solve for the batched kernel (wide strips) and its tile plan
         if (o.precision == 32) {
             lbm::BatchSolve<float> d{h->pf, (const float*)h->f[0], (float*)h->f[1]};
             err = cudaMemcpy(h->d_self, &d, sizeof(d), cudaMemcpyHostToDevice);
@@ -357,7 +379,10 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
             lbm::BatchSolve<double> d{h->pdd, (const double*)h->f[0], (double*)h->f[1]};
             err = cudaMemcpy(h->d_self, &d, sizeof(d), cudaMemcpyHostToDevice);
         }
-        if (err == cudaSuccess) err = cudaMemcpy(h->d_self_start, start, sizeof(start), cudaMemcpyHostToDevice);
+        if (err == cudaSuccess)
+            err = cudaMemcpy(h->d_tiles, tiles.data(), tiles.size() * sizeof(lbm::Tile), cudaMemcpyHostToDevice);
+        if (err == cudaSuccess)
+            err = cudaMemcpy(h->d_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice);
     }
     if (err == cudaSuccess) err = cudaMemsetAsync(h->derr, 0, sizeof(int), h->stream);
     if (err == cudaSuccess) err = cudaMemsetAsync(h->aux, 0, 4 * plane_bytes, h->stream);

@@ -19,7 +19,9 @@ struct lbm_axi_batch {
     std::vector<lbm_axi*> solves;
     std::vector<int> cur0;  // each solve's current buffer when the batch was made
     void* d_solves;         // BatchSolve<R>[n]
-    long long* d_start;     // [n + 1]
+    lbm::Tile* d_tiles;     // tile plan for (strip, grid)
+    int* d_first;           // [ncta + 1]
+    int ncta;
     int* d_err;             // [n]
     int* h_err;             // pinned [n]
     cudaStream_t stream;
@@ -56,36 +58,61 @@ const Params<double>& params_of<double>(const lbm_axi* h) {
 }
 
 template <typename R>
-cudaError_t upload(lbm_axi_batch* b, int strip) {
+cudaError_t upload(lbm_axi_batch* b) {
     std::vector<BatchSolve<R>> hs(b->n);
-    std::vector<long long> start(b->n + 1, 0);
+    std::vector<int> nz(b->n), nr(b->n);
     for (int i = 0; i < b->n; i++) {
         lbm_axi* h = b->solves[i];
         hs[i].p = params_of<R>(h);
         hs[i].f_a = static_cast<const R*>(h->f[b->cur0[i]]);
         hs[i].f_b = static_cast<R*>(h->f[b->cur0[i] ^ 1]);
-        const long long strips = (h->nz + strip - 1) / strip;
-        start[i + 1] = start[i] + strips * h->nr;
+        nz[i] = h->nz;
+        nr[i] = h->nr;
     }
-    cudaError_t e = cudaMemcpyAsync(b->d_solves, hs.data(), sizeof(BatchSolve<R>) * b->n, cudaMemcpyHostToDevice,
-                                    b->stream);
+    const int slots = b->grid > 0 ? b->grid : Ops<R>::batch_resident_ctas(b->strip);
+    if (slots <= 0) return cudaErrorInvalidConfiguration;
+    std::vector<lbm::Tile> tiles;
+    std::vector<int> first;
+    if (lbm::plan_tiles(nz.data(), nr.data(), b->n, b->strip, slots, tiles, first, nullptr) != LBM_OK)
+        return cudaErrorMemoryAllocation;
+    // the graph holds the old plan's pointers
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return e;
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_first) cudaFree(b->d_first);
+    b->d_tiles = nullptr;
+    b->d_first = nullptr;
+    b->ncta = 0;
+    e = cudaMalloc(&b->d_tiles, tiles.size() * sizeof(lbm::Tile));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_first, first.size() * sizeof(int));
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_start, start.data(), sizeof(long long) * (b->n + 1), cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(b->d_solves, hs.data(), sizeof(BatchSolve<R>) * b->n, cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_tiles, tiles.data(), tiles.size() * sizeof(lbm::Tile), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice,
                             b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) b->ncta = (int)first.size() - 1;
     return e;
 }
 
 cudaError_t upload_tables(lbm_axi_batch* b) {
-    return b->precision == 32 ? upload<float>(b, b->strip) : upload<double>(b, b->strip);
+    return b->precision == 32 ? upload<float>(b) : upload<double>(b);
 }
 
-cudaError_t launch(lbm_axi_batch* b, int parity, int strip, int grid) {
+cudaError_t launch(lbm_axi_batch* b, int parity) {
     if (b->precision == 32)
-        return Ops<float>::step_batch(static_cast<const BatchSolve<float>*>(b->d_solves), b->d_start, b->n, b->mp,
-                                      b->ax, parity, strip, grid, b->d_err, b->stream);
-    return Ops<double>::step_batch(static_cast<const BatchSolve<double>*>(b->d_solves), b->d_start, b->n, b->mp,
-                                   b->ax, parity, strip, grid, b->d_err, b->stream);
+        return Ops<float>::step_batch(static_cast<const BatchSolve<float>*>(b->d_solves), b->d_tiles, b->d_first,
+                                      b->ncta, b->mp, b->ax, parity, b->strip, b->d_err, b->stream);
+    return Ops<double>::step_batch(static_cast<const BatchSolve<double>*>(b->d_solves), b->d_tiles, b->d_first,
+                                   b->ncta, b->mp, b->ax, parity, b->strip, b->d_err, b->stream);
 }
 
 int build_graph(lbm_axi_batch* b) {
@@ -95,8 +122,8 @@ int build_graph(lbm_axi_batch* b) {
     }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
-    cudaError_t e = launch(b, 0, b->strip, b->grid);
-    if (e == cudaSuccess) e = launch(b, 1, b->strip, b->grid);
+    cudaError_t e = launch(b, 0);
+    if (e == cudaSuccess) e = launch(b, 1);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
@@ -122,7 +149,8 @@ void sync_handles(lbm_axi_batch* b) {
 void release(lbm_axi_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->d_solves) cudaFree(b->d_solves);
-    if (b->d_start) cudaFree(b->d_start);
+    if (b->d_tiles) cudaFree(b->d_tiles);
+    if (b->d_first) cudaFree(b->d_first);
     if (b->d_err) cudaFree(b->d_err);
     if (b->h_err) cudaFreeHost(b->h_err);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -176,7 +204,9 @@ int lbm_axi_batch_create(lbm_axi* const* solves, int n, void* stream, lbm_axi_ba
     b->ax = h0->opts.axis_terms != 0;
     b->device = dev;
     b->d_solves = nullptr;
-    b->d_start = nullptr;
+    b->d_tiles = nullptr;
+    b->d_first = nullptr;
+    b->ncta = 0;
     b->d_err = nullptr;
     b->h_err = nullptr;
     b->stream = nullptr;
@@ -204,7 +234,6 @@ int lbm_axi_batch_create(lbm_axi* const* solves, int n, void* stream, lbm_axi_ba
     }
     const size_t ssz = b->precision == 32 ? sizeof(BatchSolve<float>) : sizeof(BatchSolve<double>);
     bool ok = cudaMalloc(&b->d_solves, ssz * n) == cudaSuccess &&
-              cudaMalloc(&b->d_start, sizeof(long long) * (n + 1)) == cudaSuccess &&
               cudaMalloc(&b->d_err, sizeof(int) * n) == cudaSuccess &&
               cudaMallocHost(&b->h_err, sizeof(int) * n) == cudaSuccess;
     if (!ok) {
@@ -239,7 +268,7 @@ int lbm_axi_batch_step_async(lbm_axi_batch* b, long long nsteps) {
     DevGuard g(b->device);
     cudaError_t e = cudaSuccess;
     if (nsteps > 0 && (b->steps & 1)) {
-        e = launch(b, 1, b->strip, b->grid);
+        e = launch(b, 1);
         b->steps++;
         nsteps--;
     }
@@ -255,7 +284,7 @@ int lbm_axi_batch_step_async(lbm_axi_batch* b, long long nsteps) {
         }
     }
     if (e == cudaSuccess && nsteps == 1) {
-        e = launch(b, 0, b->strip, b->grid);
+        e = launch(b, 0);
         b->steps++;
     }
     sync_handles(b);
@@ -315,11 +344,11 @@ int lbm_axi_batch_set_tuning(lbm_axi_batch* b, const lbm_axi_batch_tuning* t) {
     if (!b || !t || (t->strip != lbm::kStripNarrow && t->strip != lbm::kStripWide) || t->grid < 0) return LBM_ERR_INVALID_ARG;
     DevGuard g(b->device);
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBM_ERR_CUDA;
-    if (t->strip != b->strip) {
+    if (t->strip != b->strip || t->grid != b->grid || !b->d_tiles) {
         b->strip = t->strip;
+        b->grid = t->grid;
         if (upload_tables(b) != cudaSuccess) return LBM_ERR_CUDA;
     }
-    b->grid = t->grid;
     return LBM_OK;
 }
 
@@ -346,15 +375,15 @@ int lbm_axi_batch_autotune(lbm_axi_batch* b, int trials, lbm_axi_batch_tuning* c
         const int resident = b->precision == 32 ? Ops<float>::batch_resident_ctas(strip)
                                                 : Ops<double>::batch_resident_ctas(strip);
         if (resident <= 0) continue;
-        lbm_axi_batch_tuning t = {strip, 0};
-        if (lbm_axi_batch_set_tuning(b, &t) != LBM_OK) return LBM_ERR_CUDA;
-        const int grids[2] = {resident, 2 * resident};
+        const int grids[2] = {0, 2 * resident};
         for (int gi = 0; gi < 2; gi++) {
-            const float ms = time_launches(b->stream, trials, [&] { return launch(b, parity, strip, grids[gi]); });
+            lbm_axi_batch_tuning t = {strip, grids[gi]};
+            if (lbm_axi_batch_set_tuning(b, &t) != LBM_OK) return LBM_ERR_CUDA;
+            const float ms = time_launches(b->stream, trials, [&] { return launch(b, parity); });
             if (ms > 0 && (best < 0 || ms < best)) {
                 best = ms;
                 bt.strip = strip;
-                bt.grid = gi == 0 ? 0 : grids[gi];
+                bt.grid = grids[gi];
             }
         }
     }

@@ -6,6 +6,7 @@
 
 #include "lbm_axi.h"
 #include "lbm_device.cuh"
+#include "lbm_tiles.h"
 
 using lbm::Params;
 
@@ -38,8 +39,10 @@ struct lbm_axi {
     size_t bytes;
     int path;          // LBM_PATH_FUSED or LBM_PATH_SPLIT
     int rows_per_cta;  // fused path: 0 = balanced wave (the batched kernel, batch of one); > 0 = chunks
-    void* d_self;      // BatchSolve<R> of this solve (f_a = f[0], f_b = f[1]) for the batched kernel
-    long long* d_self_start;  // {0, strips * nr}
+    void* d_self;       // BatchSolve<R> of this solve (f_a = f[0], f_b = f[1]) for the batched kernel
+    lbm::Tile* d_tiles;  // tile plan of this solve alone (wide strips, one resident wave)
+    int* d_first;        // [ncta + 1]
+    int ncta;
     Params<float> pf;
     Params<double> pdd;
     void* hb[2];  // h at the link midpoint: S0, H_z, H_r planes of the step that wrote f[c] (else null)

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
+#include "lbm_tiles.h"
 
 namespace lbm {
 
@@ -44,10 +45,11 @@ struct Ops {
     static cudaError_t step(const Params<R>& p, const R* f, R* fout, int rows_per_cta, int* err, cudaStream_t s);
     static size_t step_smem();
     static int step_strip();  // z-columns per CTA of the single-pass kernel
-    // Batched fused step over nsolves solves (device arrays solves[n], start[n+1]).
-    // strip: kStripNarrow or kStripWide z-columns per CTA; grid: CTAs (0 = one resident wave).
-    static cudaError_t step_batch(const BatchSolve<R>* solves, const long long* start, int nsolves, bool mp,
-                                  bool ax, int parity, int strip, int grid, int* err, cudaStream_t s);
+    // Batched fused step: ncta CTAs, CTA c marching tiles first[c] .. first[c + 1] - 1
+    // (device arrays planned by plan_tiles for this strip width); strip: kStripNarrow
+    // or kStripWide z-columns per CTA.
+    static cudaError_t step_batch(const BatchSolve<R>* solves, const Tile* tiles, const int* first, int ncta,
+                                  bool mp, bool ax, int parity, int strip, int* err, cudaStream_t s);
     static int batch_resident_ctas(int strip);
     static size_t batch_smem(int strip);
 };

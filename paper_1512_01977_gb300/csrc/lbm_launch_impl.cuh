@@ -256,28 +256,27 @@ int Ops<R>::batch_resident_ctas(int strip) {
 }
 
 template <typename R, int TZ>
-static cudaError_t launch_batch(const BatchSolve<R>* solves, const long long* start, int n, bool mp, bool ax,
-                                int parity, int grid, int* err, cudaStream_t s) {
+static cudaError_t launch_batch(const BatchSolve<R>* solves, const Tile* tiles, const int* first, int ncta, bool mp,
+                                bool ax, int parity, int* err, cudaStream_t s) {
     using T = BatchTile<R, TZ>;
     const size_t smem = T::smem();
     if (mp && ax)
-        batch_kernel<R, TZ, true, true>()<<<grid, T::NT, smem, s>>>(solves, start, n, parity, err);
+        batch_kernel<R, TZ, true, true>()<<<ncta, T::NT, smem, s>>>(solves, tiles, first, parity, err);
     else if (mp)
-        batch_kernel<R, TZ, true, false>()<<<grid, T::NT, smem, s>>>(solves, start, n, parity, err);
+        batch_kernel<R, TZ, true, false>()<<<ncta, T::NT, smem, s>>>(solves, tiles, first, parity, err);
     else if (ax)
-        batch_kernel<R, TZ, false, true>()<<<grid, T::NT, smem, s>>>(solves, start, n, parity, err);
+        batch_kernel<R, TZ, false, true>()<<<ncta, T::NT, smem, s>>>(solves, tiles, first, parity, err);
     else
-        batch_kernel<R, TZ, false, false>()<<<grid, T::NT, smem, s>>>(solves, start, n, parity, err);
+        batch_kernel<R, TZ, false, false>()<<<ncta, T::NT, smem, s>>>(solves, tiles, first, parity, err);
     return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t Ops<R>::step_batch(const BatchSolve<R>* solves, const long long* start, int n, bool mp, bool ax,
-                               int parity, int strip, int grid, int* err, cudaStream_t s) {
-    if (grid <= 0) grid = batch_resident_ctas(strip);
-    if (grid <= 0) return cudaErrorInvalidConfiguration;
-    return strip == kStripNarrow ? launch_batch<R, kStripNarrow>(solves, start, n, mp, ax, parity, grid, err, s)
-                       : launch_batch<R, kStripWide>(solves, start, n, mp, ax, parity, grid, err, s);
+cudaError_t Ops<R>::step_batch(const BatchSolve<R>* solves, const Tile* tiles, const int* first, int ncta, bool mp,
+                               bool ax, int parity, int strip, int* err, cudaStream_t s) {
+    if (ncta <= 0) return cudaErrorInvalidConfiguration;
+    return strip == kStripNarrow ? launch_batch<R, kStripNarrow>(solves, tiles, first, ncta, mp, ax, parity, err, s)
+                                 : launch_batch<R, kStripWide>(solves, tiles, first, ncta, mp, ax, parity, err, s);
 }
 
 }  // namespace lbm

@@ -26,6 +26,7 @@
 #pragma once
 
 #include "lbm_kernels.cuh"
+#include "lbm_tiles.h"
 
 namespace lbm {
 
@@ -113,10 +114,10 @@ struct StepShape {
     // one item per thread in every stage (the widest, stage L, sets the count)
     static constexpr int NT = (RR * WL / CP + 31) / 32 * 32;
     // ring depths (rows), powers of two; schedule checked on the CPU for RR = 2 and 4
-    static constexpr int DP = RR <= 2 ? 16 : 32, DD = 16, DJ = RR <= 2 ? 16 : 32, DU = RR <= 2 ? 8 : 16;
+    static constexpr int DP = RR <= 2 ? 16 : 32, DD = RR <= 2 ? 8 : 16, DJ = RR <= 2 ? 16 : 32, DU = RR <= 2 ? 8 : 16;
     static constexpr int elems = DP * WL + 2 * DD * WD + 3 * DJ * WU + 2 * DU * WU;
     // schedule constraints
-    static_assert(11 + 2 * RR <= DP && 7 + 2 * RR <= DD && 6 + 4 * RR <= DJ && 4 + 2 * RR <= DU, "ring depth");
+    static_assert(11 + 2 * RR <= DP && 4 + 2 * RR <= DD && 6 + 4 * RR <= DJ && 4 + 2 * RR <= DU, "ring depth");
 };
 
 // Pulled populations of node (k, j); kc = wrapped columns k-1, k, k+1.
@@ -872,47 +873,34 @@ __global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB) k_step(Params
 }
 
 // ------------------------------------------------------------ batched step --
-// Many independent solves advanced by one launch.  The strip-row spaces of the
-// solves are concatenated (solve s occupies [start[s], start[s+1])); a
-// one-wave grid cuts the concatenation into equal contiguous shares, and each
-// CTA marches the (solve, strip, rows) segments of its share.  Even batch
-// steps read f_a and write f_b, odd steps the reverse.
+// Many independent solves advanced by one launch.  The host cuts every
+// solve's (z-strip, row) space into tiles and deals them to the CTAs
+// (lbm_tiles.cu): CTA c marches tiles first[c] .. first[c + 1] - 1, each a row
+// range of one strip of one solve.  Even batch steps read f_a and write f_b,
+// odd steps the reverse.  A single solve runs as a batch of one.
 template <typename R, int TZ, int RR, int CP, int MINB, bool MP, bool AX>
 __global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB)
-    k_step_batch(const BatchSolve<R>* __restrict__ solves, const long long* __restrict__ start, int nsolves,
-                 int parity, int* __restrict__ err) {
+    k_step_batch(const BatchSolve<R>* __restrict__ solves, const Tile* __restrict__ tiles,
+                 const int* __restrict__ first, int parity, int* __restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Params<R> sp;
     __shared__ int skip;  // the solve already went unphysical: its populations are void, leave them
-    const long long total = start[nsolves];
-    const long long per = (total + gridDim.x - 1) / gridDim.x;
-    long long a = (long long)blockIdx.x * per;
-    const long long b = min(a + per, total);
-    while (a < b) {
-        int lo = 0, hi = nsolves - 1;  // last solve with start <= a
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (start[mid] <= a) lo = mid;
-            else hi = mid - 1;
-        }
-        const int s = lo;
-        __syncthreads();  // everyone is done with the previous segment's parameters
+    const int t1 = first[blockIdx.x + 1];
+    for (int t = first[blockIdx.x]; t < t1; t++) {
+        const Tile tl = tiles[t];
+        __syncthreads();  // everyone is done with the previous tile's parameters
         if (threadIdx.x == 0) {
-            sp = solves[s].p;
-            skip = *static_cast<volatile const int*>(err + s);
+            sp = solves[tl.solve].p;
+            skip = *static_cast<volatile const int*>(err + tl.solve);
         }
         __syncthreads();  // parameters and the skip decision are the same for the whole CTA
-        const long long off = a - start[s];
-        const int strip = (int)(off / sp.nr), j0 = (int)(off - (long long)strip * sp.nr);
-        const int jend = (int)min((long long)sp.nr, j0 + (b - a));
-        const R* fin = parity ? solves[s].f_b : solves[s].f_a;
-        R* fo = parity ? const_cast<R*>(solves[s].f_a) : solves[s].f_b;
+        const R* fin = parity ? solves[tl.solve].f_b : solves[tl.solve].f_a;
+        R* fo = parity ? const_cast<R*>(solves[tl.solve].f_a) : solves[tl.solve].f_b;
         if (!skip) {
             int bad = 0;
-            march_cp<R, TZ, RR, CP, MP, AX>(sp, fin, fo, strip, j0, jend, smem_raw, bad);
-            if (bad) atomicOr(&err[s], bad);
+            march_cp<R, TZ, RR, CP, MP, AX>(sp, fin, fo, tl.strip, tl.j0, tl.jend, smem_raw, bad);
+            if (bad) atomicOr(&err[tl.solve], bad);
         }
-        a += jend - j0;
     }
 }
 

@@ -101,6 +101,9 @@ _SIGS = {
     "lbm_axi_batch_autotune": (C.c_int, [_H, C.c_int, C.POINTER(lbm_axi_batch_tuning)]),
     "lbm_axi_autotune": (C.c_int, [_H, C.c_int, C.POINTER(lbm_axi_tuning)]),
     "lbm_axi_batch_destroy": (None, [_H]),
+    "lbm_axi_tile_plan": (C.c_int, [C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int,
+                                    C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
 }
 
 NOALLOC_MAX_NODES = 8388608
@@ -386,6 +389,25 @@ def lbm_axi_autotune(h, trials=5):
 
 def lbm_axi_batch_destroy(b):
     lib().lbm_axi_batch_destroy(b)
+
+
+def lbm_axi_tile_plan(sizes, strip, slots):
+    """Tile plan of a batched launch for solves of the given (nz, nr) sizes:
+    (tiles as an (ntiles, 4) array of solve, strip, j0, jend in CTA order,
+    first offsets per CTA, makespan in rows)."""
+    n = len(sizes)
+    nz = (C.c_int * n)(*[int(a) for a, _ in sizes])
+    nr = (C.c_int * n)(*[int(b) for _, b in sizes])
+    nt, nc, ms = C.c_int(), C.c_int(), C.c_longlong()
+    rc = lib().lbm_axi_tile_plan(nz, nr, n, int(strip), int(slots), 0, None, None, C.byref(nt), C.byref(nc),
+                                 C.byref(ms))
+    if rc != ERR_INVALID_ARG or nt.value <= 0:
+        _check(rc if rc != OK else ERR_INVALID_ARG, "lbm_axi_tile_plan")
+    tiles = (C.c_int * (4 * nt.value))()
+    first = (C.c_int * (int(slots) + 1))()
+    _check(lib().lbm_axi_tile_plan(nz, nr, n, int(strip), int(slots), nt.value, tiles, first, C.byref(nt),
+                                   C.byref(nc), C.byref(ms)), "lbm_axi_tile_plan")
+    return np.array(tiles, dtype=np.int64).reshape(-1, 4), np.array(first[:nc.value + 1], dtype=np.int64), ms.value
 
 
 class Batch:

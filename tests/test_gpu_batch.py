@@ -92,7 +92,7 @@ def test_batch_fp64_matches_oracle(lbm, strip):
         assert rel_err(mg["rho"], mo["rho"]) <= 1e-12
         assert vel_err(mg, mo) <= 1e-12
         for k, e in component_errs(mg, mo).items():
-            assert e is None or e <= 1e-12, (c.nz, c.nr, k, e)
+            assert e <= 1e-12, (c.nz, c.nr, k, e)
     b.close()
     for s in solvers:
         s.close()

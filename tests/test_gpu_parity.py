@@ -2,10 +2,10 @@
 
 FP64 bar, after the stated steps (only the rounding order differs between the
 two): max |gpu - oracle| / max |oracle| <= 1e-12 for rho and P_k; for each
-velocity component whose largest magnitude exceeds 1e-10,
-max |u_gpu - u_oracle| / max |u_oracle| <= 1e-12 for that component; and for
-the velocity vector max |u_gpu - u_oracle| / max(max |u|, 1e-3) <= 1e-12,
-which also bounds components that are zero by symmetry.  States are chosen
+velocity component c, max |u_gpu - u_oracle| / max(max |u_c|, 1e-3) <= 1e-12,
+and the same for the velocity vector.  A velocity's FP64 rounding error is
+absolute (populations of size w_i rho summed into rho u), so below 1e-3 the
+bar is the absolute 1e-15, ten units of that rounding.  States are chosen
 with disturbances large enough that the discrete force -- a difference of
 nearly equal psi values -- is not dominated by cancellation.  FP32 bars are
 per result and stated in test_gpu_fp32.py.
@@ -46,9 +46,7 @@ def _droplet_fields(case, R, du=0.0, seed=0, eps=0.0):
 def _check(mg, mo, tol=TOL64):
     errs = {k: rel_err(mg[k], mo[k]) for k in ("rho", "p")}
     errs["u"] = vel_err(mg, mo)
-    for k, e in component_errs(mg, mo).items():
-        if e is not None:
-            errs[k] = e
+    errs.update(component_errs(mg, mo))
     for k, e in errs.items():
         assert e <= tol, (k, errs)
     return errs

@@ -147,7 +147,7 @@ def test_young_laplace_sphere_over_radii(lbm):
 
 # ----------------------------------------------------- mode-2 oscillation --
 
-def _oscillation(lbm, kappa, precision=64, shape=(62, 76), steps=25000, every=100):
+def _oscillation(lbm, kappa, precision=64, shape=(62, 76), steps=25000, every=100, forcing=0):
     """Mode-2 frequency of an ellipsoidal drop (CS, T = 0.8 T_c, A = -0.152,
     tau = 1, 500 x 250, free-slip top) and the Miller-Scriven value for its
     measured radius and densities, with sigma from a planar droplet."""
@@ -155,7 +155,7 @@ def _oscillation(lbm, kappa, precision=64, shape=(62, 76), steps=25000, every=10
     eos = lbm.make_eos(lbm.EOS_CS, 0.8)
     rv0, rl0 = lbm.lbm_eos_coexistence(eos)
     # planar droplet: sigma of the scheme (no F_axis, so the same for both kappa readings)
-    s = lbm.Solver(320, 320, tau, eos=eos, A=A, precision=64, top=lbm.TOP_PERIODIC, axis=0)
+    s = lbm.Solver(320, 320, tau, eos=eos, A=A, precision=64, top=lbm.TOP_PERIODIC, axis=0, forcing=forcing)
     s.init(*I.droplet_2d(320, 320, 64, rl0, rv0), physical=True)
     s.step(30000)
     R2, _, _ = _plane_state(s.moments()["rho"])
@@ -164,7 +164,7 @@ def _oscillation(lbm, kappa, precision=64, shape=(62, 76), steps=25000, every=10
     # the spherical drop of the same volume at rest: its equilibrium radius and densities
     Ra, Rz = shape
     R0 = (Ra * Ra * Rz) ** (1 / 3)
-    s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=64, kappa=kappa)
+    s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=64, kappa=kappa, forcing=forcing)
     s.init(*I.droplet(nz, nr, R0, rl0, rv0), physical=True)
     s.step(20000)
     Rs, rl, rv = _axis_state(s.moments()["rho"])
@@ -172,7 +172,7 @@ def _oscillation(lbm, kappa, precision=64, shape=(62, 76), steps=25000, every=10
     # the ellipsoid, scaled to that radius, at rest
     k = Rs / R0
     s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=precision, kappa=kappa,
-                   rho_ref=rv if precision == 32 else 0.0)
+                   rho_ref=rv if precision == 32 else 0.0, forcing=forcing)
     s.init(*I.ellipsoid(nz, nr, Ra * k, Rz * k, rl, rv), physical=True)
     m_start = s.mass()[0]
     ts, ext, rad, dens = [], [], [], []
@@ -193,7 +193,7 @@ def _oscillation(lbm, kappa, precision=64, shape=(62, 76), steps=25000, every=10
     w_ms = O.analytic.miller_scriven_omega2(sig2d, Rm, rlm, rvm, nu, nu)
     w, c = O.analytic.fit_damped_cosine(ts, ext, w_guess=w_ms)
     return dict(omega=w, decay=c, omega_ms=w_ms, err=w / w_ms - 1, R=Rm, sigma_2d=sig2d, mass_drift=drift,
-                ext=ext)
+                ext=ext, rho_l=rlm, rho_v=rvm)
 
 
 def test_mode2_oscillation_lattice_kappa(lbm):
@@ -306,15 +306,18 @@ def test_fig2_coexistence_curve(lbm):
         assert ev < -2e-2
 
 
-def _oscillation_vdw(lbm, kappa, tau=0.8, A=0.0, T=0.8, shape=(62, 76), steps=25000, every=100):
-    """Mode-2 frequency of an ellipsoidal drop with the paper's vdW fluid
-    (lambda = 0.01, A = 0, T = 0.8 T_c, density ratio about 9; tau = 0.8, the
-    smallest at which this drop runs from rest, the paper's being 0.7), and the
-    Miller-Scriven value for its measured radius and densities.  At this ratio
-    the large vapour volume of the 500 x 250 box evaporates a drop started at
-    the flat-interface densities (R 66 -> 46), so a first static run measures
-    the 1/R (Kelvin) shift of both densities and the drop starts from the
-    densities it has at its own radius."""
+_VDW_PREP = {}
+
+
+def _vdw_prep(lbm, kappa, tau, A, T, R0):
+    """sigma of the scheme (planar droplet) and the densities a static drop of
+    radius R0 keeps in the 500 x 250 box.  At density ratio ~9 the large vapour
+    volume evaporates a drop started at the flat-interface densities (R 66 ->
+    46), so a first static run measures the 1/R (Kelvin) shift of both
+    densities and the drop starts from the densities it has at its own radius."""
+    key = (kappa, tau, A, T, round(R0, 6))
+    if key in _VDW_PREP:
+        return _VDW_PREP[key]
     nz, nr = 500, 250
     eos = lbm.make_eos(lbm.EOS_VDW, T, lam=LAM)
     rv0, rl0 = lbm.lbm_eos_coexistence(eos)
@@ -330,8 +333,6 @@ def _oscillation_vdw(lbm, kappa, tau=0.8, A=0.0, T=0.8, shape=(62, 76), steps=25
     R2, _, _ = _plane_state(s.moments()["rho"])
     sig2d = s.pressure_jump(160, 160, R2 / 2, R2 + 12) * R2
     s.close()
-    Ra, Rz = shape
-    R0 = (Ra * Ra * Rz) ** (1 / 3)
     s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=64, kappa=kappa)
     s.init(*I.droplet(nz, nr, R0, ll, lv), physical=True)
     s.step(20000)
@@ -342,6 +343,22 @@ def _oscillation_vdw(lbm, kappa, tau=0.8, A=0.0, T=0.8, shape=(62, 76), steps=25
     s.step(20000)
     Rs, rl, rv = _axis_state(s.moments()["rho"])
     s.close()
+    _VDW_PREP[key] = (sig2d, R1, Rs, rl, rv)
+    return _VDW_PREP[key]
+
+
+def _oscillation_vdw(lbm, kappa, tau=0.8, A=0.0, T=0.8, shape=(62, 76), steps=25000, every=100):
+    """Mode-2 frequency of an ellipsoidal drop with the paper's vdW fluid
+    (lambda = 0.01, A = 0, T = 0.8 T_c, density ratio about 9; tau = 0.8, the
+    smallest at which this drop runs from rest, the paper's being 0.7), and the
+    Miller-Scriven value for its measured radius and densities.  The ellipsoid
+    (semi-axes Ra radially, Rz along z) is scaled to the equilibrium radius of
+    the static drop of equal volume and started at rest with its densities."""
+    nz, nr = 500, 250
+    eos = lbm.make_eos(lbm.EOS_VDW, T, lam=LAM)
+    Ra, Rz = shape
+    R0 = (Ra * Ra * Rz) ** (1 / 3)
+    sig2d, R1, Rs, rl, rv = _vdw_prep(lbm, kappa, tau, A, T, R0)
     k = Rs / R0
     s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=64, kappa=kappa)
     s.init(*I.ellipsoid(nz, nr, Ra * k, Rz * k, rl, rv), physical=True)
@@ -376,3 +393,146 @@ def test_mode2_oscillation_vdw(lbm):
               % (kappa, r["omega"], r["omega_ms"], r["err"], r["R"], r["R_flat_start"], r["R_equilibrated"]))
     assert abs(out[lbm.KAPPA_LATTICE]["err"]) <= 0.05
     assert -0.15 <= out[lbm.KAPPA_THERMO]["err"] <= -0.03
+
+
+# Fig. 3's four ellipsoids (aspect ratios not printed): equal volume, the
+# radius of the (62, 76) drop, Rz / Ra = 0.8, 1.1, 76/62 and 1.4.
+FIG3_SHAPES = [(66.3 * q ** (-1 / 3), 66.3 * q ** (2 / 3)) for q in (0.8, 1.1, 76 / 62, 1.4)]
+
+
+def test_fig3_four_ellipsoids_vdw(lbm):
+    """Fig. 3 (Sec. III.B): four initial ellipsoids of the paper's fluid; the
+    paper finds mode-2 frequency errors of 6 % (min) to 8 % (max) against
+    Miller-Scriven, Eq. (oscillatingfreq).  Here, per reading of the c^4 factor
+    of F_axis: with c_k^4 (the paper's statement) every shape is 3-15 % low
+    (measured 6.5-11 %, the paper's range widened by the shapes); with c_s^4
+    every shape is within 6 %; the spread over the four shapes stays within
+    6 points for either reading."""
+    out = {}
+    for kappa in (lbm.KAPPA_THERMO, lbm.KAPPA_LATTICE):
+        errs = []
+        for shape in FIG3_SHAPES:
+            r = _oscillation_vdw(lbm, kappa, shape=shape)
+            errs.append(r["err"])
+            print("Fig. 3 vdW kappa %d shape (%.1f, %.1f): omega %.4e MS %.4e err %+.4f R %.2f"
+                  % (kappa, shape[0], shape[1], r["omega"], r["omega_ms"], r["err"], r["R"]))
+        a = np.abs(errs)
+        print("Fig. 3 vdW kappa %d: |error| min %.3f max %.3f (paper: 0.06 .. 0.08)" % (kappa, a.min(), a.max()))
+        out[kappa] = errs
+    for kappa, lo, hi in ((lbm.KAPPA_THERMO, -0.15, -0.03), (lbm.KAPPA_LATTICE, -0.06, 0.06)):
+        errs = out[kappa]
+        assert all(lo <= e <= hi for e in errs), (kappa, errs)
+        assert max(errs) - min(errs) <= 0.06, (kappa, errs)
+
+
+# ------------------------------------------- Table 1: absolute values --
+
+def _slab_profile(lbm, T, A, forcing, tau=1.5, nz=256, nr=8, steps=30000):
+    """Relaxed flat interface (fully periodic box, slab normal to z), FP64:
+    the density profile along z averaged over r."""
+    eos = lbm.make_eos(lbm.EOS_VDW, T, lam=LAM)
+    rv, rl = lbm.lbm_eos_coexistence(eos)
+    s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=64, top=lbm.TOP_PERIODIC, axis=0, forcing=forcing)
+    s.init(*I.slab(nz, nr, rl, rv, width=8.0), physical=True)
+    s.step(steps)
+    rho = s.moments()["rho"].mean(axis=0)
+    s.close()
+    return rho
+
+
+def _mechanical_sigma(rho, T, A, edm):
+    """Surface tension of a flat interface as the excess of normal over
+    tangential pressure, per interface (the profile holds two).  The Taylor
+    expansion of the discrete force of Eq. (kupershtokhforcing) (exact for
+    quadratic psi, pinned on the oracle) is
+    F = 2 psi grad psi + (1/3) psi grad lap psi + (2A/3) grad psi lap psi + (2A/3) grad |grad psi|^2,
+    the divergence of a tensor with P_N - P_T = (1 - 2A)/3 psi'^2 across a flat
+    interface.  The EDM adds F F / (4 rho) to the momentum flux of the lattice
+    fluid (the second moment of its equilibrium shift is rho u1 u1 - rho u0 u0,
+    not that of the mean velocity); Guo forcing adds nothing.  So
+    sigma = int [(1 - 2A)/3 psi'^2 + F_z^2 / (4 rho)] dz (EDM), without the last term (Guo).
+    psi' by the isotropic stencil of Eq. (fifthorderaccuratefinitedifference)
+    on a z-only profile (the 4th-order central difference); F_z the discrete
+    force of Eq. (kupershtokhforcing) on that profile."""
+    p = O.Params(nz=len(rho), nr=1, eos=O.EOS_VDW, T=T, lam=LAM, A=A)
+    pk = np.array([O.core.eos_p(p, x) for x in rho])
+    psi = np.sqrt(rho / 3 - pk)
+    up, dn = np.roll(psi, -1), np.roll(psi, 1)
+    d = (2 / 3) * (up - dn) - (1 / 12) * (np.roll(psi, -2) - np.roll(psi, 2))
+    fz = A * (up * up - dn * dn) + (1 - 2 * A) * psi * (up - dn)
+    s = (1 - 2 * A) / 3 * np.sum(d * d) / 2
+    return s + (np.sum(fz * fz / (4 * rho)) / 2 if edm else 0.0)
+
+
+def _laplace_2d(lbm, T, A, forcing, n=320, R0=64, steps=40000):
+    eos = lbm.make_eos(lbm.EOS_VDW, T, lam=LAM)
+    rv, rl = lbm.lbm_eos_coexistence(eos)
+    s = lbm.Solver(n, n, 1.5, eos=eos, A=A, precision=64, top=lbm.TOP_PERIODIC, axis=0, forcing=forcing)
+    s.init(*I.droplet_2d(n, n, R0, rl, rv, width=8.0), physical=True)
+    s.step(steps)
+    R, _, _ = _plane_state(s.moments()["rho"])
+    sig = s.pressure_jump(n / 2, n / 2, R / 2, R + 24) * R
+    s.close()
+    return sig
+
+
+@pytest.mark.parametrize("A", [0.0, -0.152])
+@pytest.mark.parametrize("T", [0.7, 0.8, 0.9])
+def test_table1_sigma_mechanics_and_forcing(lbm, T, A):
+    """Where Table 1's absolute values part from this build's.  For each
+    forcing scheme the surface tension from the printed law (planar droplet,
+    dp R, vdW lambda = 0.01, tau = 1.5, FP64) is the flat interface's mechanical
+    surface tension within 5 %: with the EDM it carries the scheme's
+    F F / (4 rho) stress, about half of it, which Guo forcing (named in
+    Sec. II.A) lacks.  The printed values are reported beside both."""
+    out = {}
+    for name, forcing in (("EDM", lbm.FORCING_EDM), ("Guo", lbm.FORCING_GUO)):
+        rho = _slab_profile(lbm, T, A, forcing)
+        sm = _mechanical_sigma(rho, T, A, edm=forcing == lbm.FORCING_EDM)
+        sl = _laplace_2d(lbm, T, A, forcing)
+        out[name] = (sl, sm)
+    paper = TABLE1[(T, A)][0]
+    print("Table 1 trace T %.1f A %+.3f: sigma/lam EDM Laplace %.4f mechanical %.4f | Guo Laplace %.4f mechanical "
+          "%.4f | paper 2D %.3f | EDM/paper %.3f Guo/paper %.3f"
+          % (T, A, out["EDM"][0] / LAM, out["EDM"][1] / LAM, out["Guo"][0] / LAM, out["Guo"][1] / LAM, paper,
+             out["EDM"][0] / LAM / paper, out["Guo"][0] / LAM / paper))
+    for name, (sl, sm) in out.items():
+        assert sl / sm == pytest.approx(1.0, abs=0.05), (name, sl, sm)
+
+
+# ------------------------------------------------ Guo forcing vs the EDM --
+
+def _flat_coexistence(lbm, T, forcing, tau=1.0):
+    eos = lbm.make_eos(lbm.EOS_VDW, T, lam=LAM)
+    rv, rl = lbm.lbm_eos_coexistence(eos)
+    s = lbm.Solver(150, 16, tau, eos=eos, A=-0.152, precision=64, top=lbm.TOP_PERIODIC, axis=0, forcing=forcing)
+    s.init(*I.slab(150, 16, rl, rv, width=4.0), physical=True)
+    s.step(40000)
+    rho = s.moments()["rho"]
+    s.close()
+    return rho[:, 75].mean() / rl - 1, rho[:, 0].mean() / rv - 1
+
+
+def test_guo_vs_edm_laplace_and_oscillation(lbm):
+    """The forcing variant of Sec. II.A (Guo) beside the default EDM on the
+    coexistence pin (vdW, A = -0.152, flat interface), Young-Laplace (P9) and the
+    mode-2 oscillation (P10, CS 0.8 T_c, c_s^4 in F_axis).  A = -0.152 is
+    Kupershtokh's value for the EDM; with Guo forcing the flat-interface
+    densities leave the Maxwell construction by more, while the surface
+    tension and the oscillation frequency stay within a few per cent of the
+    EDM's.  Both schemes run every case to completion."""
+    for T in (0.6, 0.8, 0.9):
+        el_e, ev_e = _flat_coexistence(lbm, T, lbm.FORCING_EDM)
+        el_g, ev_g = _flat_coexistence(lbm, T, lbm.FORCING_GUO)
+        print("coexistence vdW T %.1f A -0.152: EDM liquid %+.2e vapour %+.2e | Guo liquid %+.2e vapour %+.2e "
+              "(of Maxwell)" % (T, el_e, ev_e, el_g, ev_g))
+        assert abs(el_e) <= 1e-3 and abs(ev_e) <= 5e-3
+        assert np.isfinite(el_g) and np.isfinite(ev_g)
+    r_e = _oscillation(lbm, lbm.KAPPA_LATTICE, steps=20000)
+    r_g = _oscillation(lbm, lbm.KAPPA_LATTICE, steps=20000, forcing=lbm.FORCING_GUO)
+    for name, r in (("EDM", r_e), ("Guo", r_g)):
+        print("CS 0.8 Tc, %s: planar sigma %.5e, mode-2 omega %.4e, Miller-Scriven %.4e, error %+.4f, "
+              "R %.2f, rho_l %.5f, rho_v %.5f" % (name, r["sigma_2d"], r["omega"], r["omega_ms"], r["err"], r["R"],
+                                                   r["rho_l"], r["rho_v"]))
+    assert abs(r_e["err"]) <= 0.05 and abs(r_g["err"]) <= 0.15
+    assert r_g["sigma_2d"] == pytest.approx(r_e["sigma_2d"], rel=0.15)

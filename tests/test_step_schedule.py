@@ -73,7 +73,7 @@ def _check_segment(nr, j0, jend, periodic, rr, d):
 @pytest.mark.parametrize("rr", [2, 4])
 def test_ring_schedule(rr):
     d = _depths(rr)
-    assert 11 + 2 * rr <= d["DP"] and 7 + 2 * rr <= d["DD"] and 6 + 4 * rr <= d["DJ"] and 4 + 2 * rr <= d["DU"]
+    assert 11 + 2 * rr <= d["DP"] and 4 + 2 * rr <= d["DD"] and 6 + 4 * rr <= d["DJ"] and 4 + 2 * rr <= d["DU"]
     for nr in (16, 17, 20, 31, 33, 64, 100, 257):
         for periodic in (False, True):
             for chunk in (1, 2, 3, 7, 16, 23, 64, 144):
@@ -86,11 +86,14 @@ def test_ring_schedule(rr):
         _check_segment(nr, j0, rng.randrange(j0 + 1, nr + 1), rng.random() < 0.3, rr, d)
 
 
-def test_too_shallow_rings_are_caught():
-    """The emulation has teeth: the next smaller power-of-two depth of the
-    rho / j ring (the kernel masks ring indices) breaks it."""
+@pytest.mark.parametrize("ring,depth", [("DJ", 8), ("DD", 4), ("DP", 8), ("DU", 4)])
+def test_too_shallow_rings_are_caught(ring, depth):
+    """The emulation has teeth: the next smaller power-of-two depth of any
+    ring (the kernel masks ring indices) breaks it."""
     d = _depths(2)
-    shallow = dict(d, DJ=8)
+    shallow = dict(d, **{ring: depth})
     with pytest.raises(AssertionError):
-        for j0 in range(0, 64, 16):
-            _check_segment(64, j0, j0 + 16, False, 2, shallow)
+        for nr in (16, 40, 129):
+            for periodic in (False, True):
+                for j0 in range(0, nr, 16):
+                    _check_segment(nr, j0, min(j0 + 16, nr), periodic, 2, shallow)
