@@ -482,9 +482,12 @@ def test_table1_sigma_mechanics_and_forcing(lbm, T, A):
     """Where Table 1's absolute values part from this build's.  For each
     forcing scheme the surface tension from the printed law (planar droplet,
     dp R, vdW lambda = 0.01, tau = 1.5, FP64) is the flat interface's mechanical
-    surface tension within 5 %: with the EDM it carries the scheme's
-    F F / (4 rho) stress, about half of it, which Guo forcing (named in
-    Sec. II.A) lacks.  The printed values are reported beside both."""
+    surface tension within 5 % (measured 0.4-0.7 % EDM, 2-4 % Guo): with the
+    EDM it carries the scheme's F F / (4 rho) stress, about half of it, which
+    Guo forcing (named in Sec. II.A) lacks.  Guo's values are Table 1's
+    printed ones within 6 % (measured -1.1 % .. +5.1 %, five of six within
+    1.5 %), the EDM's 1.46-1.90 times them: the paper's Table 1 was computed
+    with Guo forcing."""
     out = {}
     for name, forcing in (("EDM", lbm.FORCING_EDM), ("Guo", lbm.FORCING_GUO)):
         rho = _slab_profile(lbm, T, A, forcing)
@@ -498,36 +501,52 @@ def test_table1_sigma_mechanics_and_forcing(lbm, T, A):
              out["EDM"][0] / LAM / paper, out["Guo"][0] / LAM / paper))
     for name, (sl, sm) in out.items():
         assert sl / sm == pytest.approx(1.0, abs=0.05), (name, sl, sm)
+    assert out["Guo"][0] / LAM == pytest.approx(paper, rel=0.06)
+    assert out["EDM"][0] / LAM > 1.4 * paper
 
 
 # ------------------------------------------------ Guo forcing vs the EDM --
 
-def _flat_coexistence(lbm, T, forcing, tau=1.0):
+def _flat_coexistence(lbm, T, forcing, tau=1.0, steps=40000):
+    """Flat-interface densities relative to Maxwell's, or the step at which the
+    run went unphysical."""
     eos = lbm.make_eos(lbm.EOS_VDW, T, lam=LAM)
     rv, rl = lbm.lbm_eos_coexistence(eos)
     s = lbm.Solver(150, 16, tau, eos=eos, A=-0.152, precision=64, top=lbm.TOP_PERIODIC, axis=0, forcing=forcing)
     s.init(*I.slab(150, 16, rl, rv, width=4.0), physical=True)
-    s.step(40000)
+    done = 0
+    try:
+        while done < steps:
+            s.step(1000)
+            done += 1000
+    except lbm.LbmError:
+        s.close()
+        return None, done
     rho = s.moments()["rho"]
     s.close()
-    return rho[:, 75].mean() / rl - 1, rho[:, 0].mean() / rv - 1
+    return (rho[:, 75].mean() / rl - 1, rho[:, 0].mean() / rv - 1), done
 
 
 def test_guo_vs_edm_laplace_and_oscillation(lbm):
     """The forcing variant of Sec. II.A (Guo) beside the default EDM on the
-    coexistence pin (vdW, A = -0.152, flat interface), Young-Laplace (P9) and the
-    mode-2 oscillation (P10, CS 0.8 T_c, c_s^4 in F_axis).  A = -0.152 is
-    Kupershtokh's value for the EDM; with Guo forcing the flat-interface
-    densities leave the Maxwell construction by more, while the surface
-    tension and the oscillation frequency stay within a few per cent of the
-    EDM's.  Both schemes run every case to completion."""
+    coexistence pin (vdW, A = -0.152, flat interface, tau = 1), Young-Laplace
+    (P9) and the mode-2 oscillation (P10, CS 0.8 T_c, c_s^4 in F_axis).
+    A = -0.152 is Kupershtokh's value for the EDM: the EDM keeps the Maxwell
+    densities from 0.9 down to 0.6 T_c, while Guo forcing leaves them by more
+    and, at 0.6 T_c, does not keep the flat interface at all (the run goes
+    unphysical; printed).  The planar surface tension and the oscillation are
+    reported for both; Guo's sigma is the EDM's less its F F / (4 rho) stress
+    (see the Table 1 trace), so it is smaller, and its mode-2 frequency stays
+    within 15 % of Miller-Scriven's with its own sigma."""
     for T in (0.6, 0.8, 0.9):
-        el_e, ev_e = _flat_coexistence(lbm, T, lbm.FORCING_EDM)
-        el_g, ev_g = _flat_coexistence(lbm, T, lbm.FORCING_GUO)
-        print("coexistence vdW T %.1f A -0.152: EDM liquid %+.2e vapour %+.2e | Guo liquid %+.2e vapour %+.2e "
-              "(of Maxwell)" % (T, el_e, ev_e, el_g, ev_g))
-        assert abs(el_e) <= 1e-3 and abs(ev_e) <= 5e-3
-        assert np.isfinite(el_g) and np.isfinite(ev_g)
+        edm, _ = _flat_coexistence(lbm, T, lbm.FORCING_EDM)
+        guo, n_guo = _flat_coexistence(lbm, T, lbm.FORCING_GUO)
+        print("coexistence vdW T %.1f A -0.152: EDM liquid %+.2e vapour %+.2e | Guo %s"
+              % (T, edm[0], edm[1], "liquid %+.2e vapour %+.2e (of Maxwell)" % guo if guo
+                 else "unphysical by step %d" % n_guo))
+        assert abs(edm[0]) <= 1e-3 and abs(edm[1]) <= 5e-3
+        if T >= 0.8:
+            assert guo is not None
     r_e = _oscillation(lbm, lbm.KAPPA_LATTICE, steps=20000)
     r_g = _oscillation(lbm, lbm.KAPPA_LATTICE, steps=20000, forcing=lbm.FORCING_GUO)
     for name, r in (("EDM", r_e), ("Guo", r_g)):
@@ -535,4 +554,4 @@ def test_guo_vs_edm_laplace_and_oscillation(lbm):
               "R %.2f, rho_l %.5f, rho_v %.5f" % (name, r["sigma_2d"], r["omega"], r["omega_ms"], r["err"], r["R"],
                                                    r["rho_l"], r["rho_v"]))
     assert abs(r_e["err"]) <= 0.05 and abs(r_g["err"]) <= 0.15
-    assert r_g["sigma_2d"] == pytest.approx(r_e["sigma_2d"], rel=0.15)
+    assert r_g["sigma_2d"] < r_e["sigma_2d"]
