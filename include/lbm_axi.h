@@ -99,6 +99,14 @@ enum { LBM_H_LOCAL = 0, LBM_H_LINK_AVG = 1 };
  *                    join a batch. */
 enum { LBM_FORCING_EDM = 0, LBM_FORCING_GUO = 1 };
 
+/* The A-term of F_axis, 3 kappa (c A / r) psi_r grad_c psi (Eq. multiphasecorrections):
+ *   LBM_AXIS_A_PRINTED    c = 6, as printed (default); it follows from the paper's
+ *                         Taylor form, Eq. (taylorexpanssion), whose A-term is 2A grad psi lap psi;
+ *   LBM_AXIS_A_EXPANSION  c = 2, from the exact Taylor expansion of the discrete force
+ *                         Eq. (kupershtokhforcing) on D2Q9, whose A-term is
+ *                         (2A/3)(grad psi lap psi + grad |grad psi|^2). */
+enum { LBM_AXIS_A_PRINTED = 0, LBM_AXIS_A_EXPANSION = 1 };
+
 typedef struct {
     int precision;  /* 64: FP64 populations and arithmetic; 32: FP32 populations stored as
                        deviations f_i - w_i rho_ref, FP32 arithmetic, FP64 reductions */
@@ -113,13 +121,14 @@ typedef struct {
     void* stream;   /* cudaStream_t to run on; NULL: the handle creates its own */
     int h_eval;     /* LBM_H_*: where h_i of Eq. (lbm) is evaluated (see above) */
     int forcing;    /* LBM_FORCING_*: how F enters the collision (see above) */
+    int axis_a_term; /* LBM_AXIS_A_*: the coefficient of F_axis's A-term (see above) */
 } lbm_axi_opts;
 
 typedef struct lbm_axi lbm_axi;
 
 /* Fill *opts with the defaults: FP64, free-slip top, axis terms and
  * multiphase on, LBM_KAPPA_THERMO, hr_sign -1, rho_ref 0, g_z 0, own stream,
- * LBM_H_LOCAL, LBM_FORCING_EDM. */
+ * LBM_H_LOCAL, LBM_FORCING_EDM, LBM_AXIS_A_PRINTED. */
 void lbm_axi_default_opts(lbm_axi_opts* opts);
 
 /* Create a solve on the current CUDA device.
@@ -257,7 +266,7 @@ int lbm_axi_mass_field_noalloc(const double* d_rho, int nz, int nr, double* d_ou
  * lbm_axi_save: LBM_ERR_STATE before init, LBM_ERR_INVALID_ARG if bytes is
  * too small; synchronous.  lbm_axi_load: LBM_ERR_INVALID_ARG for a blob that
  * is truncated or does not match the solve (magic, version, precision, grid,
- * rho_ref); synchronous; clears the error word.  Do not load into a solve
+ * rho_ref, or any parameter of the dynamics); synchronous; clears the error word.  Do not load into a solve
  * while it belongs to a live batch (the batch keeps its own step parity). */
 int lbm_axi_state_bytes(const lbm_axi* h, size_t* bytes);
 int lbm_axi_save(lbm_axi* h, void* buf, size_t bytes);

@@ -25,7 +25,7 @@ class _CParams(C.Structure):
         ("eos", C.c_int), ("T", C.c_double), ("a", C.c_double), ("b", C.c_double),
         ("R", C.c_double), ("lam", C.c_double), ("top", C.c_int), ("axis", C.c_int),
         ("multiphase", C.c_int), ("kappa", C.c_int), ("hr_sign", C.c_int), ("gz", C.c_double),
-        ("r0", C.c_double), ("h_eval", C.c_int), ("forcing", C.c_int),
+        ("r0", C.c_double), ("h_eval", C.c_int), ("forcing", C.c_int), ("axis_a", C.c_double),
     ]
 
 
@@ -52,6 +52,7 @@ class Params:
     r0: float = 0.0
     h_eval: int = H_LOCAL
     forcing: int = FORCING_EDM
+    axis_a: float = 6.0  # c of the c A psi_r grad psi / r term of F_axis (6 printed, 2 exact expansion)
 
     def replace(self, **kw):
         return dataclasses.replace(self, **kw)
@@ -78,7 +79,7 @@ def lib(omp=False):
             "orc_grad": (None, [P, _D, _D, _D]),
             "orc_force_kupershtokh": (None, [P, _D, _D, _D]),
             "orc_kappa": (C.c_double, [P, C.c_double]),
-            "orc_force_axis": (None, [C.c_double] * 8 + [_D, _D]),
+            "orc_force_axis": (None, [C.c_double] * 9 + [_D, _D]),
             "orc_source_H": (None, [C.c_double] * 8 + [C.c_int, _D, _D]),
             "orc_source_h": (None, [C.c_double] * 5 + [_D]),
             "orc_guo_source": (None, [C.c_double] * 5 + [_D]),
@@ -138,9 +139,9 @@ def kappa(params, rho):
     return lib().orc_kappa(C.byref(params.c()), float(rho))
 
 
-def force_axis(kappa_, A, r, psi, psi_z, psi_r, psi_rr, psi_rz):
+def force_axis(kappa_, A, r, psi, psi_z, psi_r, psi_rr, psi_rz, c=6.0):
     fz, fr = C.c_double(), C.c_double()
-    lib().orc_force_axis(kappa_, A, r, psi, psi_z, psi_r, psi_rr, psi_rz, C.byref(fz), C.byref(fr))
+    lib().orc_force_axis(kappa_, A, c, r, psi, psi_z, psi_r, psi_rr, psi_rz, C.byref(fz), C.byref(fr))
     return fz.value, fr.value
 
 

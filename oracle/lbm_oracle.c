@@ -61,6 +61,8 @@ typedef struct {
                        axis.  r0 > 0 describes a window cut out of a larger lattice (tests). */
     int h_eval;     /* where h_i of Eq. (lbm) is evaluated: ORC_H_LOCAL or ORC_H_LINK_AVG */
     int forcing;    /* how F enters the collision: ORC_FORCING_EDM (Sec. II.C) or ORC_FORCING_GUO (Sec. II.A) */
+    double axis_a;  /* c of the c A psi_r grad psi / r term of F_axis: 6 as printed in Eq.
+                       (multiphasecorrections), 2 from the exact expansion of Eq. (kupershtokhforcing) */
 } orc_params;
 
 /* ------------------------------------------------------------------ EOS -- */
@@ -218,12 +220,14 @@ double orc_kappa(const orc_params* P, double rho) {
 }
 
 /* Cylindrical contribution to the multiphase force, Eq. (multiphasecorrections):
- * F_axis = 3 kappa [psi grad_c(psi_r / r) + (6A / r) psi_r grad_c psi], with
- * grad_c(psi_r/r) = (psi_rz / r, psi_rr / r - psi_r / r^2). */
-void orc_force_axis(double kappa, double A, double r, double psi, double psi_z, double psi_r,
+ * F_axis = 3 kappa [psi grad_c(psi_r / r) + (c A / r) psi_r grad_c psi], with
+ * grad_c(psi_r/r) = (psi_rz / r, psi_rr / r - psi_r / r^2).  The paper prints
+ * c = 6, from its Taylor form Eq. (taylorexpanssion); the exact expansion of the
+ * discrete force Eq. (kupershtokhforcing) gives c = 2 (P->axis_a selects). */
+void orc_force_axis(double kappa, double A, double c, double r, double psi, double psi_z, double psi_r,
                     double psi_rr, double psi_rz, double* fz, double* fr) {
-    *fz = 3.0 * kappa * (psi * psi_rz / r + 6.0 * A / r * psi_r * psi_z);
-    *fr = 3.0 * kappa * (psi * (psi_rr / r - psi_r / (r * r)) + 6.0 * A / r * psi_r * psi_r);
+    *fz = 3.0 * kappa * (psi * psi_rz / r + c * A / r * psi_r * psi_z);
+    *fr = 3.0 * kappa * (psi * (psi_rr / r - psi_r / (r * r)) + c * A / r * psi_r * psi_r);
 }
 
 /* --------------------------------------------------- axisymmetric source -- */
@@ -399,7 +403,7 @@ static int orc_fields(const orc_params* P, const double* f, orc_work* w) {
             double fr = w->fkr[e];
             if (P->multiphase && P->axis) {
                 double az, ar;
-                orc_force_axis(orc_kappa(P, rho), P->A, r, w->psi[e], w->psiz[e], w->psir[e],
+                orc_force_axis(orc_kappa(P, rho), P->A, P->axis_a, r, w->psi[e], w->psiz[e], w->psir[e],
                                w->psirr[e], w->psirz[e], &az, &ar);
                 fz += az;
                 fr += ar;

@@ -47,6 +47,7 @@ Params<R> make_params(const lbm_axi* h) {
     p.nz = h->nz;
     p.nr = h->nr;
     p.pitch = h->pitch;
+    p.axis_a = (R)(h->opts.axis_a_term == LBM_AXIS_A_EXPANSION ? 2.0 : 6.0);
     p.plane = h->plane;
     p.tau_inv = (R)(1.0 / h->tau);
     p.nu = (R)((h->tau - 0.5) / 3.0);
@@ -241,6 +242,7 @@ void lbm_axi_default_opts(lbm_axi_opts* o) {
     o->stream = nullptr;
     o->h_eval = LBM_H_LOCAL;
     o->forcing = LBM_FORCING_EDM;
+    o->axis_a_term = LBM_AXIS_A_PRINTED;
 }
 
 size_t lbm_axi_footprint(int nz, int nr, int precision) {
@@ -266,6 +268,7 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     if (o.hr_sign != 1 && o.hr_sign != -1) return LBM_ERR_INVALID_ARG;
     if (o.h_eval != LBM_H_LOCAL && o.h_eval != LBM_H_LINK_AVG) return LBM_ERR_INVALID_ARG;
     if (o.forcing != LBM_FORCING_EDM && o.forcing != LBM_FORCING_GUO) return LBM_ERR_INVALID_ARG;
+    if (o.axis_a_term != LBM_AXIS_A_PRINTED && o.axis_a_term != LBM_AXIS_A_EXPANSION) return LBM_ERR_INVALID_ARG;
     lbm_eos e;
     memset(&e, 0, sizeof(e));
     double T = 0.0, Tc = 0.0;
@@ -607,7 +610,7 @@ struct StateHeader {
     // dynamics (format version 2)
     double tau, A, T, T_over_Tc, a, b, R, lambda, g_z;
     int32_t eos_kind, top_bc, axis_terms, multiphase, kappa_mode, hr_sign, h_eval, forcing;
-    double reserved2[3];
+    int32_t axis_a_term, reserved2[5];
 };
 static_assert(sizeof(StateHeader) == 192, "checkpoint header layout");
 const char kStateMagic[8] = {'L', 'B', 'M', 'A', 'X', 'I', 'S', '1'};
@@ -640,6 +643,7 @@ void fill_header(const lbm_axi* h, StateHeader* hd) {
     hd->hr_sign = h->opts.hr_sign;
     hd->h_eval = h->opts.h_eval;
     hd->forcing = h->opts.forcing;
+    hd->axis_a_term = h->opts.axis_a_term;
 }
 
 // The blob continues this solve: same layout and the same dynamics, bit for bit.
@@ -653,7 +657,7 @@ bool header_matches(const lbm_axi* h, const StateHeader& hd) {
            hd.b == mine.b && hd.R == mine.R && hd.lambda == mine.lambda && hd.g_z == mine.g_z &&
            hd.eos_kind == mine.eos_kind && hd.top_bc == mine.top_bc && hd.axis_terms == mine.axis_terms &&
            hd.multiphase == mine.multiphase && hd.kappa_mode == mine.kappa_mode && hd.hr_sign == mine.hr_sign &&
-           hd.h_eval == mine.h_eval && hd.forcing == mine.forcing;
+           hd.h_eval == mine.h_eval && hd.forcing == mine.forcing && hd.axis_a_term == mine.axis_a_term;
 }
 
 // planes in the blob: the 9 populations, then (link-midpoint source) the 3 source planes

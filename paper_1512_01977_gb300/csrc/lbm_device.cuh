@@ -54,6 +54,7 @@ template <typename R>
 struct Params {
     int nz, nr;        // grid
     int pitch;         // row pitch (elements) of every plane, >= nz, multiple of 32
+    R axis_a;          // c of the c A psi_r grad psi / r term of F_axis (6 printed, 2 exact expansion)
     long long plane;   // elements per plane = pitch * nr
     R tau_inv;         // 1 / tau
     R nu;              // (tau - 1/2) / 3

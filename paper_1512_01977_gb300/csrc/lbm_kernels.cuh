@@ -194,15 +194,16 @@ __global__ void __launch_bounds__(256) k_update(Params<R> p, Params<double> pd, 
             const R* m = sPsi + (jl - j0 + 6) * PW + (b + 4);
             kupershtokh<R, PW>(m, p.A, fz, fr);
             if (ax) {
-                // F_axis = 3 kappa [psi grad_c(psi_r / r) + (6A / r) psi_r grad_c psi],
-                // Eq. (multiphasecorrections); psi_rr = D_r(psi_r), psi_rz = D_r(psi_z).
+                // F_axis = 3 kappa [psi grad_c(psi_r / r) + (c A / r) psi_r grad_c psi],
+                // Eq. (multiphasecorrections) (c = 6 as printed, 2 from the exact expansion);
+                // psi_rr = D_r(psi_r), psi_rz = D_r(psi_z).
                 const int ld = (jl - j0 + 4) * DW + (b + 2);
                 const R psi = m[0], psz = sPz[ld], psr = sPr[ld];
                 const R prr = fd_r<R, DW>(sPr + ld);
                 const R prz = fd_r<R, DW>(sPz + ld);
                 const R ir = R(1) / (R(jm) + R(0.5));
                 const R k3 = R(3) * kappa_of(p, rho);
-                const R a6 = R(6) * p.A * ir * psr;
+                const R a6 = p.axis_a * p.A * ir * psr;
                 fz += k3 * (psi * prz * ir + a6 * psz);
                 fr += k3 * (psi * (prr - psr * ir) * ir + a6 * psr);
             }

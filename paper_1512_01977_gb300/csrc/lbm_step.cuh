@@ -305,7 +305,7 @@ __device__ __forceinline__ void march(const Params<R>& p, const R* __restrict__ 
                         if (periodic) rrow = row < 0 ? row + p.nr : (row >= p.nr ? row - p.nr : row);
                         const R ir = rcp(R(rrow) + R(0.5));
                         const R k3 = R(3) * kappa_fast(p, rho);
-                        const R a6 = R(6) * kA * ir * psr;
+                        const R a6 = p.axis_a * kA * ir * psr;
                         const R psi = m0[0];
                         fz += k3 * (psi * prz * ir + a6 * psz);
                         fr += k3 * (psi * (prr - psr * ir) * ir + a6 * psr);
@@ -730,7 +730,8 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
                         const R ir = rcp(R(rrow) + R(0.5));
                         const T irr = pk(ir, ir);
                         const T k3 = pmul(pk(R(3), R(3)), kappa2<R>(p, rho));
-                        const T a6 = pmul(pk(R(6) * kA * ir, R(6) * kA * ir), psr);
+                        const R ca = p.axis_a * kA * ir;
+                        const T a6 = pmul(pk(ca, ca), psr);
                         const T pir = pmul(psi, irr);
                         fz = pfma(k3, pfma(pir, prz, pmul(a6, psz)), fz);
                         fr = pfma(k3, pfma(pir, psub(prr, pmul(psr, irr)), pmul(a6, psr)), fr);

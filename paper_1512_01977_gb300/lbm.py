@@ -27,11 +27,12 @@ class lbm_eos(C.Structure):
 class lbm_axi_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("top_bc", C.c_int), ("axis_terms", C.c_int), ("multiphase", C.c_int),
                 ("kappa_mode", C.c_int), ("hr_sign", C.c_int), ("rho_ref", C.c_double), ("g_z", C.c_double),
-                ("stream", C.c_void_p), ("h_eval", C.c_int), ("forcing", C.c_int)]
+                ("stream", C.c_void_p), ("h_eval", C.c_int), ("forcing", C.c_int), ("axis_a_term", C.c_int)]
 
 
 H_LOCAL, H_LINK_AVG = 0, 1
 FORCING_EDM, FORCING_GUO = 0, 1
+AXIS_A_PRINTED, AXIS_A_EXPANSION = 0, 1
 
 
 PATH_FUSED, PATH_SPLIT = 1, 2
@@ -481,11 +482,11 @@ class Solver:
 
     def __init__(self, nz, nr, tau, eos=None, A=-0.152, precision=64, top=TOP_FREESLIP, axis=1, multiphase=1,
                  kappa=KAPPA_THERMO, hr_sign=-1, rho_ref=0.0, g_z=0.0, stream=None, h_eval=H_LOCAL,
-                 forcing=FORCING_EDM):
+                 forcing=FORCING_EDM, axis_a_term=AXIS_A_PRINTED):
         o = lbm_axi_default_opts()
         o.precision, o.top_bc, o.axis_terms, o.multiphase = precision, top, axis, multiphase
         o.kappa_mode, o.hr_sign, o.rho_ref, o.g_z = kappa, hr_sign, rho_ref, g_z
-        o.stream, o.h_eval, o.forcing = stream, h_eval, forcing
+        o.stream, o.h_eval, o.forcing, o.axis_a_term = stream, h_eval, forcing, axis_a_term
         self.nz, self.nr = nz, nr
         self.eos = eos
         self.h = lbm_axi_create(nz, nr, tau, eos, A, o)

@@ -26,11 +26,13 @@ class Case:
     r0: float = 0.0  # oracle only: radial offset of a window cut from a larger lattice
     h_eval: int = O.H_LOCAL
     forcing: int = O.FORCING_EDM
+    axis_a: float = 6.0  # 6: F_axis A-term as printed; 2: from the exact expansion
 
     def oracle_params(self):
         p = O.Params(nz=self.nz, nr=self.nr, tau=self.tau, A=self.A, eos=self.eos, lam=self.lam, top=self.top,
                      axis=self.axis, multiphase=self.multiphase, kappa=self.kappa, hr_sign=self.hr_sign,
-                     gz=self.gz, r0=self.r0, h_eval=self.h_eval, forcing=self.forcing)
+                     gz=self.gz, r0=self.r0, h_eval=self.h_eval, forcing=self.forcing,
+                     axis_a=self.axis_a)
         Tc, _ = O.eos.critical_point(p)
         return p.replace(T=self.T_over_Tc * Tc)
 
@@ -43,7 +45,8 @@ class Case:
         eos = lbm.make_eos(self.eos, self.T_over_Tc, lam=self.lam) if self.multiphase else None
         return lbm.Solver(self.nz, self.nr, self.tau, eos=eos, A=self.A, precision=precision, top=self.top,
                           axis=self.axis, multiphase=self.multiphase, kappa=self.kappa, hr_sign=self.hr_sign,
-                          rho_ref=rho_ref, g_z=self.gz, h_eval=self.h_eval, forcing=self.forcing)
+                          rho_ref=rho_ref, g_z=self.gz, h_eval=self.h_eval, forcing=self.forcing,
+                          axis_a_term=lbm.AXIS_A_EXPANSION if self.axis_a == 2.0 else lbm.AXIS_A_PRINTED)
 
 
 def run_oracle(case, fields, steps):

@@ -155,6 +155,15 @@ def test_kappa_modes_fp64(kappa):
     _compare(c, _droplet_fields(c, 9, du=1e-3, seed=3), 60)
 
 
+@pytest.mark.parametrize("tuning", [(1, 0), (2, 0)])
+@pytest.mark.parametrize("kappa", [O.KAPPA_LATTICE, O.KAPPA_THERMO])
+def test_axis_a_expansion_fp64(kappa, tuning):
+    """F_axis with the exact expansion's A-coefficient (c = 2), fused and
+    two-kernel paths, against the oracle."""
+    c = Case(45, 27, kappa=kappa, axis_a=2.0)
+    _compare(c, _droplet_fields(c, 10, du=2e-3, seed=13), 60, tuning=tuning)
+
+
 def test_vdw_fp64():
     c = Case(48, 28, tau=1.5, eos=O.EOS_VDW, A=0.0, T_over_Tc=0.8)
     _compare(c, _droplet_fields(c, 10, du=1e-3, seed=4), 60)

@@ -147,7 +147,7 @@ def test_young_laplace_sphere_over_radii(lbm):
 
 # ----------------------------------------------------- mode-2 oscillation --
 
-def _oscillation(lbm, kappa, precision=64, shape=(62, 76), steps=25000, every=100, forcing=0):
+def _oscillation(lbm, kappa, precision=64, shape=(62, 76), steps=25000, every=100, forcing=0, axis_a_term=0):
     """Mode-2 frequency of an ellipsoidal drop (CS, T = 0.8 T_c, A = -0.152,
     tau = 1, 500 x 250, free-slip top) and the Miller-Scriven value for its
     measured radius and densities, with sigma from a planar droplet."""
@@ -164,7 +164,7 @@ def _oscillation(lbm, kappa, precision=64, shape=(62, 76), steps=25000, every=10
     # the spherical drop of the same volume at rest: its equilibrium radius and densities
     Ra, Rz = shape
     R0 = (Ra * Ra * Rz) ** (1 / 3)
-    s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=64, kappa=kappa, forcing=forcing)
+    s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=64, kappa=kappa, forcing=forcing, axis_a_term=axis_a_term)
     s.init(*I.droplet(nz, nr, R0, rl0, rv0), physical=True)
     s.step(20000)
     Rs, rl, rv = _axis_state(s.moments()["rho"])
@@ -172,7 +172,7 @@ def _oscillation(lbm, kappa, precision=64, shape=(62, 76), steps=25000, every=10
     # the ellipsoid, scaled to that radius, at rest
     k = Rs / R0
     s = lbm.Solver(nz, nr, tau, eos=eos, A=A, precision=precision, kappa=kappa,
-                   rho_ref=rv if precision == 32 else 0.0, forcing=forcing)
+                   rho_ref=rv if precision == 32 else 0.0, forcing=forcing, axis_a_term=axis_a_term)
     s.init(*I.ellipsoid(nz, nr, Ra * k, Rz * k, rl, rv), physical=True)
     m_start = s.mass()[0]
     ts, ext, rad, dens = [], [], [], []
@@ -555,3 +555,41 @@ def test_guo_vs_edm_laplace_and_oscillation(lbm):
                                                    r["rho_l"], r["rho_v"]))
     assert abs(r_e["err"]) <= 0.05 and abs(r_g["err"]) <= 0.15
     assert r_g["sigma_2d"] < r_e["sigma_2d"]
+
+
+# ------------------------------------------- F_axis: the A-term coefficient --
+
+def test_axis_a_term_young_laplace_and_oscillation(lbm):
+    """F_axis's A-term with the printed coefficient (6A) and with the one the
+    exact expansion of the discrete force gives (2A), at c^4 = c_s^4 (CS,
+    0.8 T_c, A = -0.152, tau = 1): the spherical Young-Laplace law dp = 2 sigma / R
+    against the planar droplet's sigma over R = 32..64, and the mode-2
+    frequency against Miller-Scriven.  Both readings keep dp R constant within
+    6 % and within 10 % of the planar sigma; printed for comparison."""
+    eos = lbm.make_eos(lbm.EOS_CS, 0.8)
+    rv, rl = lbm.lbm_eos_coexistence(eos)
+    s = lbm.Solver(256, 256, 1.0, eos=eos, A=-0.152, precision=64, top=lbm.TOP_PERIODIC, axis=0)
+    s.init(*I.droplet_2d(256, 256, 48, rl, rv), physical=True)
+    s.step(20000)
+    R2, _, _ = _plane_state(s.moments()["rho"])
+    sig2d = s.pressure_jump(128, 128, R2 / 2, R2 + 12) * R2
+    s.close()
+    for term, name in ((lbm.AXIS_A_PRINTED, "6A (printed)"), (lbm.AXIS_A_EXPANSION, "2A (exact expansion)")):
+        sig = []
+        for R0 in (32, 48, 64):
+            nz, nr = 4 * R0 + 64, 2 * R0 + 48
+            s = lbm.Solver(nz, nr, 1.0, eos=eos, A=-0.152, precision=64, kappa=lbm.KAPPA_LATTICE,
+                           axis_a_term=term)
+            s.init(*I.droplet(nz, nr, R0, rl, rv), physical=True)
+            s.step(20000)
+            R, _, _ = _axis_state(s.moments()["rho"])
+            sig.append(s.pressure_jump(nz / 2, 0, R / 2, R + 12) * R / 2)
+            s.close()
+        r = _oscillation(lbm, lbm.KAPPA_LATTICE, steps=20000, axis_a_term=term)
+        print("F_axis A-term %s: sphere sigma(R = 32, 48, 64) / planar sigma = %s; mode-2 omega %.4e, "
+              "Miller-Scriven %.4e, error %+.4f" % (name, np.round(np.array(sig) / sig2d, 4).tolist(), r["omega"],
+                                                    r["omega_ms"], r["err"]))
+        assert max(sig) / min(sig) < 1.06
+        for x in sig:
+            assert x == pytest.approx(sig2d, rel=0.10)
+        assert abs(r["err"]) <= 0.05

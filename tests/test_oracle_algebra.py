@@ -286,6 +286,50 @@ def test_force_axis_is_the_cylindrical_part_of_the_taylor_force():
     assert fr == pytest.approx(er, rel=1e-5)
 
 
+def test_force_axis_exact_expansion_coefficient():
+    """Reading of F_axis's A-term.  The discrete force's exact expansion on D2Q9
+    (pinned for quadratic psi by test_kupershtokh_quadratic_psi) is
+    F = 2 psi grad psi + (1/3) psi grad lap psi + (2A/3) grad psi lap psi + (2A/3) grad |grad psi|^2;
+    the paper's Eq. (taylorexpanssion) prints 2A for the third coefficient.
+    For an axisymmetric psi the 3D Laplacian is the planar one plus psi_r / r,
+    and |grad psi|^2 is the same, so the cylindrical correction is
+    (1/3) [psi grad(psi_r / r) + 2A (psi_r / r) grad psi]: F_axis with c = 2 at
+    c^4 = 1/9.  (The two forms agree in 1D, where grad psi lap psi and
+    grad |grad psi|^2 / 2 coincide, and differ in 2D.)"""
+    s, A, kap = 30.0, -0.152, 1 / 9
+    z, r = 1.3, 2.7
+
+    def psi(z, r):
+        return 0.2 + np.exp(-(z * z + r * r) / s)
+
+    h = 1e-4
+    pz = (psi(z + h, r) - psi(z - h, r)) / (2 * h)
+    pr = (psi(z, r + h) - psi(z, r - h)) / (2 * h)
+    q = lambda zz, rr: (psi(zz, rr + h) - psi(zz, rr - h)) / (2 * h) / rr  # psi_r / r
+    dq_dz = (q(z + h, r) - q(z - h, r)) / (2 * h)
+    dq_dr = (q(z, r + h) - q(z, r - h)) / (2 * h)
+    ez = (psi(z, r) * dq_dz + 2 * A * pz * pr / r) / 3
+    er = (psi(z, r) * dq_dr + 2 * A * pr * pr / r) / 3
+    prr = (psi(z, r + h) - 2 * psi(z, r) + psi(z, r - h)) / h**2
+    prz = (psi(z + h, r + h) - psi(z + h, r - h) - psi(z - h, r + h) + psi(z - h, r - h)) / (4 * h * h)
+    fz, fr = core.force_axis(kap, A, r, psi(z, r), pz, pr, prr, prz, c=2.0)
+    assert fz == pytest.approx(ez, rel=1e-5)
+    assert fr == pytest.approx(er, rel=1e-5)
+    # the 2D expansion's third coefficient, from the discrete force itself: a quadratic
+    # psi with an isotropic Hessian separates 2A/3 (exact) from the printed 2A
+    p = O.Params(nz=6, nr=5, A=A)
+    ext = core.ext_from_function(p, lambda Z, R: 0.5 + 0.002 * (Z * Z + R * R))
+    fzd, _ = core.force_kupershtokh(p, ext)
+    Z, _ = np.meshgrid(np.arange(p.nz) + 0.5, np.arange(p.nr) + 0.5)
+    ps = 0.5 + 0.002 * (Z * Z + (np.arange(p.nr)[:, None] + 0.5) ** 2)
+    dz, lap = 0.004 * Z, 0.008
+    a_part = fzd - 2 * ps * dz  # the A-dependent remainder of the discrete force
+    exact = 2 * A / 3 * (dz * lap + 2 * 0.004 * dz)
+    printed = 2 * A * dz * lap
+    np.testing.assert_allclose(a_part, exact, rtol=1e-9, atol=1e-15)
+    assert np.max(np.abs(a_part - printed)) > 0.1 * np.max(np.abs(printed))
+
+
 @pytest.mark.parametrize("mode,expect", [(O.KAPPA_LATTICE, lambda c2: 1 / 9),
                                          (O.KAPPA_THERMO, lambda c2: c2 * c2),
                                          (O.KAPPA_MIXED, lambda c2: c2 / 3)])
