@@ -414,7 +414,7 @@ def run_ours(args):
     extra = {}
     if ws == 1 and args.blocks:
         # the batched and served workloads, bounded, on the same GPU after the headline
-        extra["batched"] = _batched_block(steps=200, warmup=3)
+        extra["batched"] = _batched_block(steps=1000, warmup=3)
         extra["served"] = _served_block(rates=(100,), requests=24, budget_mb=4096)
     if rank == 0:
         cpu = None
