@@ -20,7 +20,7 @@ extern "C" {
 
 typedef struct lbm_axi_batch lbm_axi_batch;
 
-/* strip: z-columns per CTA, 64 or 96; grid: CTA slots the tiles are dealt to,
+/* strip: z-columns per CTA, 64 or 112; grid: CTA slots the tiles are dealt to,
  * 0 = one wave of resident CTAs. */
 typedef struct {
     int strip;
@@ -58,7 +58,7 @@ int lbm_axi_batch_get_tuning(const lbm_axi_batch* b, lbm_axi_batch_tuning* t);
 int lbm_axi_batch_set_tuning(lbm_axi_batch* b, const lbm_axi_batch_tuning* t);
 
 /* Autotuner: time `trials` launches of every candidate configuration (strip
- * 64 / 96 x tiles dealt to one or two resident waves) on this batch, keep the
+ * 64 / 112 x tiles dealt to one or two resident waves) on this batch, keep the
  * fastest and return it in *chosen (may be NULL).  Non-destructive: trial
  * launches read the current populations and write only the buffer the next
  * step overwrites; error words raised by trials are cleared.  Synchronous. */

@@ -13,7 +13,10 @@ constexpr int kReduceBlocks = 304;  // 2 x 152 SMs; fixed so reductions are repr
 constexpr int kStepMinRows = 16;    // the single-pass kernel needs single reflections at the walls
 // z-columns per CTA of the two compiled forms of the batched kernel (the wide
 // one is the default; the autotuner may pick the narrow one for small grids).
-constexpr int kStripNarrow = 64, kStripWide = 96;
+// 112: with 128 threads of two columns each, stages L, D, U and C fill 124,
+// 120, 116 and 112 of them, and strip origins stay 64-byte aligned; measured
+// fastest of the even widths 96 ... 116 on the 4096 x 2048 wave.
+constexpr int kStripNarrow = 64, kStripWide = 112;
 
 template <typename R>
 struct Ops {

@@ -45,7 +45,7 @@ struct StepTile;
 // CP: columns per thread (2: march2, pairs of nodes with packed FP32 arithmetic).
 template <>
 struct StepTile<float> {
-    static constexpr int TZ = 96, RR = 2, CP = 2, MINB = 4;  // 128 threads, 45.8 KB of rings
+    static constexpr int TZ = 112, RR = 2, CP = 2, MINB = 4;  // 128 threads, 45.3 KB of rings
 };
 template <>
 struct StepTile<double> {
@@ -191,8 +191,8 @@ namespace lbm {
 // Batched kernel forms: strip width kStripNarrow or kStripWide (the autotuner picks), force and
 // axis terms compiled in or out.
 // Resident CTAs per SM the launch bounds ask for: what shared memory allows at
-// each width (FP32 two columns per thread: 45.8 KB / 31.5 KB of rings; FP64
-// one column: 91.6 KB / 63 KB).
+// each width (FP32 two columns per thread: 45.3 KB / 26.9 KB of rings; FP64
+// one column: 90.6 KB / 53.8 KB).
 template <typename R, int TZ>
 struct BatchMinBlocks {
     static constexpr int value = sizeof(R) == 4 ? (TZ == kStripWide ? 4 : 5) : (TZ == kStripWide ? 2 : 3);
