@@ -79,12 +79,14 @@ enum {
  *   LBM_H_LOCAL     at the node, h_i(x, t) (default; every path);
  *   LBM_H_LINK_AVG  the mean of the link's two end nodes at time t: h_i(x)/2 at
  *                   the collision and h_i(y)/2 at the arrival node y, for the
- *                   direction the population arrives with.  Two-kernel path only
- *                   (the solve is created on it, the fused path is refused and
- *                   such a solve cannot join a batch); keeps two extra sets of
- *                   three planes.  Its radial acoustic modes decay at about
- *                   0.7 nu k^2 instead of nu k^2: the half-link shift has no
- *                   matching half-step in time. */
+ *                   direction the population arrives with.  Keeps two extra sets
+ *                   of three planes (24 B per node more traffic per FP32 step).
+ *                   The fused path has it with the force and the axis terms on
+ *                   (balanced wave only, rows_per_cta = 0); otherwise the solve
+ *                   runs the two-kernel path.  Such a solve cannot join a batch.
+ *                   Its radial acoustic modes decay at about 0.7 nu k^2 instead
+ *                   of nu k^2: the half-link shift has no matching half-step in
+ *                   time. */
 enum { LBM_H_LOCAL = 0, LBM_H_LINK_AVG = 1 };
 
 /* How the force F enters the collision of Eq. (lbm):
@@ -94,9 +96,10 @@ enum { LBM_H_LOCAL = 0, LBM_H_LINK_AVG = 1 };
  *   LBM_FORCING_GUO  Guo forcing (Sec. II.A): f^eq at the fluid velocity
  *                    u = u0 + F/(2 rho) and S_i = w_i (1 - 1/(2 tau)) [(c_i - u).F / c_s^2
  *                    + (c_i.u)(c_i.F) / c_s^4] (the printed second term, (c_i - u).(c_i - F),
- *                    is read as Guo's (c_i.u)(c_i.F)).  Two-kernel path only, like
- *                    LBM_H_LINK_AVG: the fused path refuses it and such a solve cannot
- *                    join a batch. */
+ *                    is read as Guo's (c_i.u)(c_i.F)).  Like LBM_H_LINK_AVG: on the
+ *                    fused path with the force and the axis terms on (rows_per_cta
+ *                    = 0), else on the two-kernel path; such a solve cannot join a
+ *                    batch. */
 enum { LBM_FORCING_EDM = 0, LBM_FORCING_GUO = 1 };
 
 /* The A-term of F_axis, 3 kappa (c A / r) psi_r grad_c psi (Eq. multiphasecorrections):
@@ -199,10 +202,12 @@ int lbm_axi_time_kernels(lbm_axi* h, long long n, double* ms);
  *         (z-strip, row) space (default); > 0 -- fixed chunks of that many rows
  *         of one z-strip per CTA.
  * The default is FUSED (nr >= 16) with rows_per_cta = 0; a solve with
- * h_eval = LBM_H_LINK_AVG or forcing = LBM_FORCING_GUO is SPLIT only.  The paths
- * agree to rounding.  Setting waits for the handle's stream; it returns
- * LBM_ERR_INVALID_ARG for an unknown path, rows_per_cta < 0, or FUSED when
- * nr < 16, with LBM_H_LINK_AVG or with LBM_FORCING_GUO. */
+ * h_eval = LBM_H_LINK_AVG or forcing = LBM_FORCING_GUO defaults to FUSED only
+ * when multiphase and axis_terms are both on (else SPLIT).  The paths agree to
+ * rounding.  Setting waits for the handle's stream; it returns
+ * LBM_ERR_INVALID_ARG for an unknown path, rows_per_cta < 0, FUSED when nr < 16,
+ * and FUSED for a LBM_H_LINK_AVG or LBM_FORCING_GUO solve without both switches
+ * or with rows_per_cta > 0. */
 enum { LBM_PATH_FUSED = 1, LBM_PATH_SPLIT = 2 };
 typedef struct {
     int path;

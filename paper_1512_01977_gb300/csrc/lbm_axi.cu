@@ -39,6 +39,17 @@ int pitch_of(int nz) { return (nz + 31) / 32 * 32; }
 
 #include "lbm_handle.h"
 
+// The balanced one-wave grid: the batched kernel with a batch of one, so a
+// solve runs the same code alone as inside any batch.
+cudaError_t lbm_handle_step_tiles(lbm_axi* h, int c) {
+    const bool mp = h->opts.multiphase != 0, ax = h->opts.axis_terms != 0;
+    if (h->precision == 32)
+        return Ops<float>::step_batch(static_cast<const lbm::BatchSolve<float>*>(h->d_self), h->d_tiles, h->d_first,
+                                      h->ncta, mp, ax, c, lbm::kStripWide, h->derr, h->stream, fv_of(h));
+    return Ops<double>::step_batch(static_cast<const lbm::BatchSolve<double>*>(h->d_self), h->d_tiles, h->d_first,
+                                   h->ncta, mp, ax, c, lbm::kStripWide, h->derr, h->stream, fv_of(h));
+}
+
 namespace {
 
 template <typename R>
@@ -80,23 +91,13 @@ double stored_rho_ref(const lbm_axi* h) {
     return h->precision == 32 ? (double)(float)h->opts.rho_ref : h->opts.rho_ref;
 }
 
-int cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
-
 // One step.  Fused path: kernel (b') reads f[cur] and writes f[cur^1].  Split
 // path: kernel (a) on the current populations, kernel (b) into the other buffer.
 cudaError_t enqueue_step(lbm_axi* h) {
     const int c = h->cur;
     cudaError_t e;
     if (h->path == LBM_PATH_FUSED && h->rows_per_cta == 0) {
-        // balanced one-wave grid: the batched kernel with a batch of one, so a
-        // solve runs the same code alone as inside any batch
-        const bool mp = h->opts.multiphase != 0, ax = h->opts.axis_terms != 0;
-        if (h->precision == 32)
-            e = Ops<float>::step_batch(static_cast<const lbm::BatchSolve<float>*>(h->d_self), h->d_tiles,
-                                       h->d_first, h->ncta, mp, ax, c, lbm::kStripWide, h->derr, h->stream);
-        else
-            e = Ops<double>::step_batch(static_cast<const lbm::BatchSolve<double>*>(h->d_self), h->d_tiles,
-                                        h->d_first, h->ncta, mp, ax, c, lbm::kStripWide, h->derr, h->stream);
+        e = lbm_handle_step_tiles(h, c);
         h->cur = c ^ 1;
         return e;
     }
@@ -367,8 +368,7 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     }
     h->pf = make_params<float>(h);
     h->pdd = make_params<double>(h);
-    // the link-midpoint source and Guo forcing are implemented on the two-kernel path only
-    h->path = nr >= lbm::kStepMinRows && !split_only(h) ? LBM_PATH_FUSED : LBM_PATH_SPLIT;
+    h->path = fused_ok(h) ? LBM_PATH_FUSED : LBM_PATH_SPLIT;
     h->rows_per_cta = 0;  // balanced single wave
     if (h->precision == 32) h->pdd = make_params_out(h);
     *h->herr = 0;
@@ -376,10 +376,12 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     {
         // descriptor of this solve for the batched kernel (wide strips) and its tile plan
         if (o.precision == 32) {
-            lbm::BatchSolve<float> d{h->pf, (const float*)h->f[0], (float*)h->f[1]};
+            lbm::BatchSolve<float> d{h->pf, (const float*)h->f[0], (float*)h->f[1], (const float*)h->hb[0],
+                                     (float*)h->hb[1]};
             err = cudaMemcpy(h->d_self, &d, sizeof(d), cudaMemcpyHostToDevice);
         } else {
-            lbm::BatchSolve<double> d{h->pdd, (const double*)h->f[0], (double*)h->f[1]};
+            lbm::BatchSolve<double> d{h->pdd, (const double*)h->f[0], (double*)h->f[1], (const double*)h->hb[0],
+                                      (double*)h->hb[1]};
             err = cudaMemcpy(h->d_self, &d, sizeof(d), cudaMemcpyHostToDevice);
         }
         if (err == cudaSuccess)
@@ -780,7 +782,8 @@ int lbm_axi_get_tuning(const lbm_axi* h, lbm_axi_tuning* t) {
 int lbm_axi_set_tuning(lbm_axi* h, const lbm_axi_tuning* t) {
     if (!h || !t) return LBM_ERR_INVALID_ARG;
     if (t->path != LBM_PATH_FUSED && t->path != LBM_PATH_SPLIT) return LBM_ERR_INVALID_ARG;
-    if (t->path == LBM_PATH_FUSED && (h->nr < lbm::kStepMinRows || split_only(h))) return LBM_ERR_INVALID_ARG;
+    if (t->path == LBM_PATH_FUSED && !fused_ok(h)) return LBM_ERR_INVALID_ARG;
+    if (t->path == LBM_PATH_FUSED && fv_of(h) != 0 && t->rows_per_cta != 0) return LBM_ERR_INVALID_ARG;
     if (t->rows_per_cta < 0 || t->rows_per_cta > (1 << 20)) return LBM_ERR_INVALID_ARG;
     DeviceGuard g(h->device);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LBM_ERR_CUDA;

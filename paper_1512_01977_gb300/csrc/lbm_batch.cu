@@ -191,7 +191,7 @@ int lbm_axi_batch_create(lbm_axi* const* solves, int n, void* stream, lbm_axi_ba
         const lbm_axi* h = solves[i];
         if (!h || !h->initialized || h->device != dev || h->precision != h0->precision ||
             h->nr < lbm::kStepMinRows || h->opts.multiphase != h0->opts.multiphase ||
-            h->opts.axis_terms != h0->opts.axis_terms || split_only(h))  // (two-kernel-only options)
+            h->opts.axis_terms != h0->opts.axis_terms || unbatchable(h))
             return LBM_ERR_INVALID_ARG;
         for (int k = 0; k < i; k++)
             if (solves[k] == h) return LBM_ERR_INVALID_ARG;
@@ -428,10 +428,14 @@ int lbm_axi_autotune(lbm_axi* h, int trials, lbm_axi_tuning* chosen) {
         }
         return e;
     };
-    if (h->nr >= lbm::kStepMinRows && !split_only(h)) {  // the fused forms lack these options
+    if (fused_ok(h)) {
+        // rows 0: the balanced wave (a batch of one, the form every collision variant has)
         const int rows_list[5] = {0, 32, 64, 144, 256};
-        for (int q = 0; q < 5; q++) {
-            const float ms = time_launches(h->stream, trials, [&] { return fused(rows_list[q]); });
+        const int nrows = fv_of(h) ? 1 : 5;
+        for (int q = 0; q < nrows; q++) {
+            const float ms = time_launches(h->stream, trials, [&] {
+                return rows_list[q] == 0 ? lbm_handle_step_tiles(h, c) : fused(rows_list[q]);
+            });
             if (ms > 0 && (best < 0 || ms < best)) {
                 best = ms;
                 bt.path = LBM_PATH_FUSED;

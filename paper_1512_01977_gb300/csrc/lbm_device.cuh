@@ -66,7 +66,7 @@ struct Params {
     int top, axis, multiphase, kappa, hr_sign;
 };
 
-// h_i at the link midpoint (two-kernel path only): the step that reads the
+// h_i at the link midpoint: the step that reads the
 // populations adds the arrival half h_i(y)/2 from src (the S0 = -rho u_r/r,
 // H_z, H_r planes of the step that wrote them) and writes its own to dst.
 // Null pointers: h_i at the node.
@@ -77,13 +77,21 @@ struct LinkPlanes {
 };
 
 // One solve of a batched launch: its parameters and its two population buffers
-// (even batch steps read f_a and write f_b, odd steps the reverse).
+// (even batch steps read f_a and write f_b, odd steps the reverse), and with
+// the link-midpoint source its two sets of source planes, swapped the same way
+// (null otherwise).
 template <typename R>
 struct BatchSolve {
     Params<R> p;
     const R* f_a;
     R* f_b;
+    const R* h_a;
+    R* h_b;
 };
+
+// Compiled forms of the collision in the fused kernel (bit set): Guo forcing
+// in place of the EDM shift, the link-midpoint source in place of h_i at the node.
+enum { FV_GUO = 1, FV_LINK = 2 };
 
 // --------------------------------------------------------------------- EOS --
 // P_k(rho) of Eq. (kupershtokvdwpressure) or Carnahan-Starling.

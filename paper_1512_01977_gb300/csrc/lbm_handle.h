@@ -6,6 +6,7 @@
 
 #include "lbm_axi.h"
 #include "lbm_device.cuh"
+#include "lbm_launch.h"
 #include "lbm_tiles.h"
 
 using lbm::Params;
@@ -39,7 +40,8 @@ struct lbm_axi {
     size_t bytes;
     int path;          // LBM_PATH_FUSED or LBM_PATH_SPLIT
     int rows_per_cta;  // fused path: 0 = balanced wave (the batched kernel, batch of one); > 0 = chunks
-    void* d_self;       // BatchSolve<R> of this solve (f_a = f[0], f_b = f[1]) for the batched kernel
+                       // (EDM with h_i at the node only)
+    void* d_self;       // BatchSolve<R> of this solve (f_a = f[0], f_b = f[1], h_a = hb[0], h_b = hb[1])
     lbm::Tile* d_tiles;  // tile plan of this solve alone (wide strips, one resident wave)
     int* d_first;        // [ncta + 1]
     int ncta;
@@ -56,10 +58,21 @@ inline lbm::LinkPlanes<R> link_planes(const lbm_axi* h, int c) {
     return {static_cast<const R*>(h->hb[c]), static_cast<R*>(h->hb[c ^ 1])};
 }
 
-// Guo forcing in place of the EDM shift (two-kernel path only).
+// Guo forcing in place of the EDM shift.
 inline bool guo_of(const lbm_axi* h) { return h->opts.forcing == LBM_FORCING_GUO; }
-// Options that only the two-kernel path implements (no fused step, no batch).
-inline bool split_only(const lbm_axi* h) { return h->hb[0] != nullptr || guo_of(h); }
+// Collision form of the fused kernel (lbm::FV_* bits): Guo forcing, link-midpoint source.
+inline int fv_of(const lbm_axi* h) { return (guo_of(h) ? lbm::FV_GUO : 0) | (h->hb[0] ? lbm::FV_LINK : 0); }
+// The fused kernel runs this solve: nr >= kStepMinRows, and the Guo and link-source
+// forms are compiled with the force and the axis terms on only.
+inline bool fused_ok(const lbm_axi* h) {
+    return h->nr >= lbm::kStepMinRows && (fv_of(h) == 0 || (h->opts.multiphase && h->opts.axis_terms));
+}
+// Options the batched engine lacks (such a solve cannot join a batch).
+inline bool unbatchable(const lbm_axi* h) { return fv_of(h) != 0; }
+
+// One fused step of this solve as a batch of one (its tile plan, the collision
+// form fv_of(h)) reading f[c] and writing f[c^1]; enqueued on h->stream.
+cudaError_t lbm_handle_step_tiles(lbm_axi* h, int c);
 
 // Step parity bookkeeping used by the batch API: after n steps run outside
 // the handle's own step loop, its current buffer flips when n is odd.

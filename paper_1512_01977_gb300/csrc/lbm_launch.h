@@ -50,9 +50,10 @@ struct Ops {
     static int step_strip();  // z-columns per CTA of the single-pass kernel
     // Batched fused step: ncta CTAs, CTA c marching tiles first[c] .. first[c + 1] - 1
     // (device arrays planned by plan_tiles for this strip width); strip: kStripNarrow
-    // or kStripWide z-columns per CTA.
+    // or kStripWide z-columns per CTA.  fv: FV_* collision form, nonzero only with
+    // kStripWide and mp && ax (cudaErrorInvalidValue otherwise).
     static cudaError_t step_batch(const BatchSolve<R>* solves, const Tile* tiles, const int* first, int ncta,
-                                  bool mp, bool ax, int parity, int strip, int* err, cudaStream_t s);
+                                  bool mp, bool ax, int parity, int strip, int* err, cudaStream_t s, int fv = 0);
     static int batch_resident_ctas(int strip);
     static size_t batch_smem(int strip);
 };

@@ -207,9 +207,9 @@ struct BatchTile {
     static size_t smem() { return sizeof(R) * (size_t)StepShape<TZ, RR, CP>::elems; }
 };
 
-template <typename R, int TZ, bool MP, bool AX>
+template <typename R, int TZ, bool MP, bool AX, int FV = 0>
 static auto batch_kernel() {
-    return k_step_batch<R, TZ, BatchTile<R, TZ>::RR, BatchTile<R, TZ>::CP, BatchTile<R, TZ>::MINB, MP, AX>;
+    return k_step_batch<R, TZ, BatchTile<R, TZ>::RR, BatchTile<R, TZ>::CP, BatchTile<R, TZ>::MINB, MP, AX, FV>;
 }
 
 template <typename R, int TZ>
@@ -226,6 +226,17 @@ static cudaError_t batch_prepare() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(batch_kernel<R, TZ, false, false>(),
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if constexpr (TZ == kStripWide) {  // the collision variants (Guo, link source): wide strips, force + axis
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batch_kernel<R, TZ, true, true, FV_GUO>(),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batch_kernel<R, TZ, true, true, FV_LINK>(),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(batch_kernel<R, TZ, true, true, FV_GUO | FV_LINK>(),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    }
     return e;
 }
 
@@ -257,9 +268,26 @@ int Ops<R>::batch_resident_ctas(int strip) {
 
 template <typename R, int TZ>
 static cudaError_t launch_batch(const BatchSolve<R>* solves, const Tile* tiles, const int* first, int ncta, bool mp,
-                                bool ax, int parity, int* err, cudaStream_t s) {
+                                bool ax, int fv, int parity, int* err, cudaStream_t s) {
     using T = BatchTile<R, TZ>;
     const size_t smem = T::smem();
+    if (fv != 0) {
+        if constexpr (TZ == kStripWide) {
+            if (!(mp && ax)) return cudaErrorInvalidValue;
+            if (fv == FV_GUO)
+                batch_kernel<R, TZ, true, true, FV_GUO>()<<<ncta, T::NT, smem, s>>>(solves, tiles, first, parity, err);
+            else if (fv == FV_LINK)
+                batch_kernel<R, TZ, true, true, FV_LINK>()<<<ncta, T::NT, smem, s>>>(solves, tiles, first, parity, err);
+            else if (fv == (FV_GUO | FV_LINK))
+                batch_kernel<R, TZ, true, true, FV_GUO | FV_LINK>()<<<ncta, T::NT, smem, s>>>(solves, tiles, first,
+                                                                                           parity, err);
+            else
+                return cudaErrorInvalidValue;
+            return cudaGetLastError();
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     if (mp && ax)
         batch_kernel<R, TZ, true, true>()<<<ncta, T::NT, smem, s>>>(solves, tiles, first, parity, err);
     else if (mp)
@@ -273,10 +301,11 @@ static cudaError_t launch_batch(const BatchSolve<R>* solves, const Tile* tiles, 
 
 template <typename R>
 cudaError_t Ops<R>::step_batch(const BatchSolve<R>* solves, const Tile* tiles, const int* first, int ncta, bool mp,
-                               bool ax, int parity, int strip, int* err, cudaStream_t s) {
+                               bool ax, int parity, int strip, int* err, cudaStream_t s, int fv) {
     if (ncta <= 0) return cudaErrorInvalidConfiguration;
-    return strip == kStripNarrow ? launch_batch<R, kStripNarrow>(solves, tiles, first, ncta, mp, ax, parity, err, s)
-                                 : launch_batch<R, kStripWide>(solves, tiles, first, ncta, mp, ax, parity, err, s);
+    return strip == kStripNarrow
+               ? launch_batch<R, kStripNarrow>(solves, tiles, first, ncta, mp, ax, fv, parity, err, s)
+               : launch_batch<R, kStripWide>(solves, tiles, first, ncta, mp, ax, fv, parity, err, s);
 }
 
 }  // namespace lbm

@@ -143,11 +143,23 @@ __device__ __forceinline__ void prefetch(const Params<R>& p, const R* __restrict
     if (valid) gather32(p, f, j, kc, fi);
 }
 
+// The three source planes (S0, H_z, H_r) of the link-midpoint source at node (k, j).
+template <typename R>
+__device__ __forceinline__ void link3(const Params<R>& p, const R* __restrict__ h, int j, int k, R (&a)[3]) {
+    const int o = j * p.pitch + k, plane = (int)p.plane;
+    a[0] = h[o];
+    a[1] = h[plane + o];
+    a[2] = h[2 * plane + o];
+}
+
 // One CTA marches z-strip `strip` over rows [j0, jend).  MP / AX: pseudopotential
-// force and axisymmetric terms compiled in or out.
-template <typename R, int TZ, int RR, bool MP, bool AX>
+// force and axisymmetric terms compiled in or out.  FV: collision form (FV_GUO:
+// Guo forcing; FV_LINK: h_i as the link average, reading the previous step's
+// source planes from hsrc and writing this step's to hdst).
+template <typename R, int TZ, int RR, bool MP, bool AX, int FV = 0>
 __device__ __forceinline__ void march(const Params<R>& p, const R* __restrict__ f, R* __restrict__ fout, int strip,
-                                      int j0, int jend, unsigned char* smem_raw, int& bad) {
+                                      int j0, int jend, unsigned char* smem_raw, int& bad,
+                                      const R* __restrict__ hsrc = nullptr, R* __restrict__ hdst = nullptr) {
     using S = StepShape<TZ, RR>;
     constexpr int WL = S::WL, WD = S::WD, WU = S::WU, LAG = S::LAG;
     constexpr int DP = S::DP, DD = S::DD, DJ = S::DJ, DU = S::DU;
@@ -206,13 +218,18 @@ __device__ __forceinline__ void march(const Params<R>& p, const R* __restrict__ 
     auto c_valid = [&](int row) { return row >= j0 && row < jend; };
 
     R lpf[Q], cpf[Q];  // populations gathered one iteration ahead (stage L, stage C)
+    R lpa[3] = {R(0), R(0), R(0)}, cpa[3] = {R(0), R(0), R(0)};  // link source planes, likewise
+    constexpr bool link = (FV & FV_LINK) != 0, guo = (FV & FV_GUO) != 0;
     {
         int sg;
         const int row = j0 - 6 + l_rr;
         const bool v = l_valid(row);
-        prefetch(p, f, v, v ? lsrc(row, sg) : 0, lkc, lpf);
+        const int jm = v ? lsrc(row, sg) : 0;
+        prefetch(p, f, v, jm, lkc, lpf);
+        if (link && v) link3(p, hsrc, jm, lkc[1], lpa);
         const int crw = j0 - 6 - 3 * LAG + c_rr;
         prefetch(p, f, c_valid(crw), crw, ckc, cpf);
+        if (link && c_valid(crw)) link3(p, hsrc, crw, ckc[1], cpa);
     }
 
     for (int pb = j0 - 6; pb - 3 * LAG < jend; pb += RR) {
@@ -223,9 +240,15 @@ __device__ __forceinline__ void march(const Params<R>& p, const R* __restrict__ 
                 int sgn_r;
                 lsrc(row, sgn_r);
                 const R d1 = lpf[1] + lpf[5] + lpf[7], d2 = lpf[2] + lpf[6] + lpf[8];
-                const R drho = lpf[0] + lpf[3] + lpf[4] + d1 + d2;
-                const R jz = d1 - d2;
-                const R jr = (lpf[3] + lpf[5] + lpf[8]) - (lpf[4] + lpf[6] + lpf[7]);
+                R drho = lpf[0] + lpf[3] + lpf[4] + d1 + d2;
+                R jz = d1 - d2;
+                R jr = (lpf[3] + lpf[5] + lpf[8]) - (lpf[4] + lpf[6] + lpf[7]);
+                if (link) {
+                    // arrival halves h_i(y)/2: zeroth moment S0/2, first moment H/2
+                    drho += R(0.5) * lpa[0];
+                    jz += R(0.5) * lpa[1];
+                    jr += R(0.5) * lpa[2];
+                }
                 const R rho = p.rho_ref + drho;
                 if (mp) {
                     const R arg = rho * (R(1) / R(3)) - eos_p_fast(p, rho);
@@ -245,7 +268,9 @@ __device__ __forceinline__ void march(const Params<R>& p, const R* __restrict__ 
             int sg;
             const int nrow = row + RR;
             const bool nv = l_valid(nrow);  // (inactive items sit far out of range: no map_row for them)
-            prefetch(p, f, nv, nv ? lsrc(nrow, sg) : 0, lkc, lpf);
+            const int njm = nv ? lsrc(nrow, sg) : 0;
+            prefetch(p, f, nv, njm, lkc, lpf);
+            if (link && nv) link3(p, hsrc, njm, lkc[1], lpa);
         }
 
         // ---- stage D: rows pb-LAG ..: psi_z, psi_r (only with F_axis).
@@ -324,7 +349,9 @@ __device__ __forceinline__ void march(const Params<R>& p, const R* __restrict__ 
             R fi[Q];
 #pragma unroll
             for (int i = 0; i < Q; i++) fi[i] = cpf[i];
+            const R a0 = cpa[0], az = cpa[1], ar = cpa[2];
             prefetch(p, f, c_valid(row + RR), row + RR, ckc, cpf);  // next iteration's gather
+            if (link && c_valid(row + RR)) link3(p, hsrc, row + RR, ckc[1], cpa);
             if (c_valid(row)) {
                 const int c = cc + 2;
                 const int sj = (row & (DJ - 1)) * WU + c;
@@ -357,20 +384,53 @@ __device__ __forceinline__ void march(const Params<R>& p, const R* __restrict__ 
                 //   even = w [omega drho + rho (q(u1) - (1 - omega) q(u0)) + m0],
                 //          q(u) = 4.5 (c.u)^2 - 1.5 u.u
                 //   odd  = 3 w [rho ((c.u1) - (1 - omega)(c.u0)) + c.H]
-                const R u0sq = u0z * u0z + u0r * u0r, u1sq = u1z * u1z + u1r * u1r;
-                const R base = omega * drho + rho * (om1 * R(1.5) * u0sq - R(1.5) * u1sq);
                 const int o = row * p.pitch + k0 + cc;
-                fout[o] = om1 * fi[0] + w_of<R>(0) * (base + m0);
+                // link-midpoint source: this node's arrival half of the previous step's
+                // h_i and the departure half of this step's; S0, H kept for the next step
+                const R hs = link ? R(0.5) : R(1);
+                const R hm0 = hs * m0, hHz = hs * Hz, hHr = hs * Hr;
+                if (link) {
 #pragma unroll
-                for (int m = 0; m < 4; m++) {
-                    const int i = 2 * m + 1;  // i and i+1 are opposite
-                    const R w = w_of<R>(i);
-                    const R cx = R(cz_of(i)), cy = R(cr_of(i));
-                    const R cu0 = cx * u0z + cy * u0r, cu1 = cx * u1z + cy * u1r;
-                    const R even = w * (base + rho * R(4.5) * (cu1 * cu1 - om1 * cu0 * cu0) + m0);
-                    const R odd = R(3) * w * (rho * (cu1 - om1 * cu0) + cx * Hz + cy * Hr);
-                    fout[i * plane + o] = om1 * fi[i] + even + odd;
-                    fout[(i + 1) * plane + o] = om1 * fi[i + 1] + even - odd;
+                    for (int i = 0; i < Q; i++)
+                        fi[i] += R(0.5) * w_of<R>(i) * (a0 + R(3) * (R(cz_of(i)) * az + R(cr_of(i)) * ar));
+                    hdst[o] = m0;
+                    hdst[plane + o] = Hz;
+                    hdst[2 * plane + o] = Hr;
+                }
+                if (guo) {
+                    // Guo forcing: f*_i = f_i + omega (f^eq_i(u) - f_i) + S_i + h_i with
+                    // S_i = w_i (1 - omega/2) [3 (c_i - u).F + 9 (c_i.u)(c_i.F)], F = 2 rho (u - u0)
+                    const R Fz = R(2) * rho * (uz - u0z), Fr = R(2) * rho * (ur - u0r);
+                    const R usq = uz * uz + ur * ur, uF = uz * Fz + ur * Fr;
+                    const R gpre = R(1) - R(0.5) * omega;
+                    const R base = omega * (drho - R(1.5) * rho * usq) - gpre * R(3) * uF + hm0;
+                    fout[o] = om1 * fi[0] + w_of<R>(0) * base;
+#pragma unroll
+                    for (int m = 0; m < 4; m++) {
+                        const int i = 2 * m + 1;
+                        const R w = w_of<R>(i);
+                        const R cx = R(cz_of(i)), cy = R(cr_of(i));
+                        const R cu = cx * uz + cy * ur, cF = cx * Fz + cy * Fr;
+                        const R even = w * (base + R(4.5) * omega * rho * cu * cu + gpre * R(9) * cu * cF);
+                        const R odd = R(3) * w * (omega * rho * cu + gpre * cF + cx * hHz + cy * hHr);
+                        fout[i * plane + o] = om1 * fi[i] + even + odd;
+                        fout[(i + 1) * plane + o] = om1 * fi[i + 1] + even - odd;
+                    }
+                } else {
+                    const R u0sq = u0z * u0z + u0r * u0r, u1sq = u1z * u1z + u1r * u1r;
+                    const R base = omega * drho + rho * (om1 * R(1.5) * u0sq - R(1.5) * u1sq);
+                    fout[o] = om1 * fi[0] + w_of<R>(0) * (base + hm0);
+#pragma unroll
+                    for (int m = 0; m < 4; m++) {
+                        const int i = 2 * m + 1;  // i and i+1 are opposite
+                        const R w = w_of<R>(i);
+                        const R cx = R(cz_of(i)), cy = R(cr_of(i));
+                        const R cu0 = cx * u0z + cy * u0r, cu1 = cx * u1z + cy * u1r;
+                        const R even = w * (base + rho * R(4.5) * (cu1 * cu1 - om1 * cu0 * cu0) + hm0);
+                        const R odd = R(3) * w * (rho * (cu1 - om1 * cu0) + cx * hHz + cy * hHr);
+                        fout[i * plane + o] = om1 * fi[i] + even + odd;
+                        fout[(i + 1) * plane + o] = om1 * fi[i + 1] + even - odd;
+                    }
                 }
             }
         }
@@ -569,9 +629,26 @@ __device__ __forceinline__ void gather2(const Params<R>& p, const R* __restrict_
     }
 }
 
-template <typename R, int TZ, int RR, bool MP, bool AX>
+// The link source planes at nodes (k, j) and (k+1, j) (k+1 wrapped in z).
+template <typename R, typename T>
+__device__ __forceinline__ void link2(const Params<R>& p, const R* __restrict__ h, int j, int k, bool contig,
+                                      T (&a)[3]) {
+    const int plane = (int)p.plane;
+    const R* b = h + j * p.pitch;
+    if (contig) {
+#pragma unroll
+        for (int q = 0; q < 3; q++) a[q] = ld2<T>(b + q * plane, k);
+    } else {
+        const int k1 = wrap_small(k + 1, p.nz);
+#pragma unroll
+        for (int q = 0; q < 3; q++) a[q] = pk(b[q * plane + k], b[q * plane + k1]);
+    }
+}
+
+template <typename R, int TZ, int RR, bool MP, bool AX, int FV = 0>
 __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__ f, R* __restrict__ fout, int strip,
-                                       int j0, int jend, unsigned char* smem_raw, int& bad) {
+                                       int j0, int jend, unsigned char* smem_raw, int& bad,
+                                       const R* __restrict__ hsrc = nullptr, R* __restrict__ hdst = nullptr) {
     using S = StepShape<TZ, RR, 2>;
     using T = typename PairOf<R>::T;
     constexpr int WL = S::WL, WD = S::WD, WU = S::WU, LAG = S::LAG;
@@ -634,12 +711,25 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
     auto c_valid = [&](int row) { return row >= j0 && row < jend; };
 
     T lpf[Q], cpf[Q];  // populations gathered one iteration ahead (stage L, stage C)
+    T lpa[3], cpa[3];  // link source planes, likewise (FV_LINK)
+    constexpr bool link = (FV & FV_LINK) != 0, guo = (FV & FV_GUO) != 0;
+    if (link) {
+#pragma unroll
+        for (int q = 0; q < 3; q++) lpa[q] = cpa[q] = pk(R(0), R(0));
+    }
     {
         int sg;
         const int row = j0 - 6 + l_rr;
-        if (l_valid(row)) gather2<false>(p, f, lsrc(row, sg), lk, l_contig, lpf);
+        if (l_valid(row)) {
+            const int jm = lsrc(row, sg);
+            gather2<false>(p, f, jm, lk, l_contig, lpf);
+            if (link) link2<R>(p, hsrc, jm, lk, l_contig, lpa);
+        }
         const int crw = j0 - 6 - 3 * LAG + c_rr;
-        if (c_valid(crw)) gather2<kStreamC>(p, f, crw, ck, c_contig, cpf);
+        if (c_valid(crw)) {
+            gather2<kStreamC>(p, f, crw, ck, c_contig, cpf);
+            if (link) link2<R>(p, hsrc, crw, ck, c_contig, cpa);
+        }
     }
 
     for (int pb = j0 - 6; pb - 3 * LAG < jend; pb += RR) {
@@ -650,9 +740,16 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
                 int sgn_r;
                 lsrc(row, sgn_r);
                 const T d1 = padd(padd(lpf[1], lpf[5]), lpf[7]), d2 = padd(padd(lpf[2], lpf[6]), lpf[8]);
-                const T drho = padd(padd(padd(lpf[0], lpf[3]), padd(lpf[4], d1)), d2);
-                const T jz = psub(d1, d2);
-                const T jr = psub(padd(padd(lpf[3], lpf[5]), lpf[8]), padd(padd(lpf[4], lpf[6]), lpf[7]));
+                T drho = padd(padd(padd(lpf[0], lpf[3]), padd(lpf[4], d1)), d2);
+                T jz = psub(d1, d2);
+                T jr = psub(padd(padd(lpf[3], lpf[5]), lpf[8]), padd(padd(lpf[4], lpf[6]), lpf[7]));
+                if (link) {
+                    // arrival halves h_i(y)/2: zeroth moment S0/2, first moment H/2
+                    const T half = pk(R(0.5), R(0.5));
+                    drho = pfma(half, lpa[0], drho);
+                    jz = pfma(half, lpa[1], jz);
+                    jr = pfma(half, lpa[2], jr);
+                }
                 const T rho = padd(drho, pk(rho_ref, rho_ref));
                 if (mp) {
                     const T arg = psub(pmul(rho, pk(R(1) / R(3), R(1) / R(3))), eos_p2<R>(p, rho));
@@ -671,7 +768,11 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
             // issue the next iteration's gather now; it lands behind this iteration's arithmetic
             int sg;
             const int nrow = row + RR;
-            if (l_valid(nrow)) gather2<false>(p, f, lsrc(nrow, sg), lk, l_contig, lpf);
+            if (l_valid(nrow)) {
+                const int jm = lsrc(nrow, sg);
+                gather2<false>(p, f, jm, lk, l_contig, lpf);
+                if (link) link2<R>(p, hsrc, jm, lk, l_contig, lpa);
+            }
         }
 
         // ---- stage D: psi_z, psi_r (only with F_axis).
@@ -750,10 +851,17 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
         // ---- stage C: collide and store.
         {
             const int row = pb - 3 * LAG + c_rr;
-            T fi[Q];
+            T fi[Q], ca[3];
 #pragma unroll
             for (int i = 0; i < Q; i++) fi[i] = cpf[i];
-            if (c_valid(row + RR)) gather2<kStreamC>(p, f, row + RR, ck, c_contig, cpf);  // next iteration's gather
+            if (link) {
+#pragma unroll
+                for (int q = 0; q < 3; q++) ca[q] = cpa[q];
+            }
+            if (c_valid(row + RR)) {  // next iteration's gather
+                gather2<kStreamC>(p, f, row + RR, ck, c_contig, cpf);
+                if (link) link2<R>(p, hsrc, row + RR, ck, c_contig, cpa);
+            }
             if (c_valid(row)) {
                 const int c = cc + 2;
                 const int sj = (row & (DJ - 1)) * WU;
@@ -786,48 +894,90 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
                 // f*_i = (1 - omega) f_i + f^eq_i(u1) - (1 - omega) f^eq_i(u0) + h_i, opposite
                 // directions sharing the even part (see march)
                 const T om1p = pk(om1, om1), c15 = pk(R(1.5), R(1.5)), c45 = pk(R(4.5), R(4.5));
-                const T u0sq = pfma(u0z, u0z, pmul(u0r, u0r)), u1sq = pfma(u1z, u1z, pmul(u1r, u1r));
-                const T base = pfma(pk(omega, omega), drho, pmul(rho, pmul(c15, psub(pmul(om1p, u0sq), u1sq))));
                 R* o = fout + row * pitch + k0 + cc;
-                auto store = [&](int i, T v) {
+                auto store_to = [&](R* q, int i, T v) {
                     if (kStreamStore) {
                         if (c_v1)
-                            __stcs(reinterpret_cast<T*>(o + i * plane), v);
+                            __stcs(reinterpret_cast<T*>(q + i * plane), v);
                         else
-                            __stcs(o + i * plane, v.x);
+                            __stcs(q + i * plane, v.x);
                     } else {
                         if (c_v1)
-                            st2(o + i * plane, 0, v);
+                            st2(q + i * plane, 0, v);
                         else
-                            o[i * plane] = v.x;
+                            q[i * plane] = v.x;
                     }
                 };
-                store(0, pfma(om1p, fi[0], pmul(pk(w_of<R>(0), w_of<R>(0)), padd(base, m0))));
-#pragma unroll
-                for (int m = 0; m < 4; m++) {
-                    const int i = 2 * m + 1;  // i and i+1 are opposite
-                    const R w = w_of<R>(i);
+                auto store = [&](int i, T v) { store_to(o, i, v); };
+                // c_i . v for the first direction of opposite pair i, i+1 (i odd)
+                auto cdot = [&](int i, T vz, T vr) {
                     const int cx = cz_of(i), cy = cr_of(i);
-                    T cu0, cu1, cH;
-                    if (cy == 0) {
-                        cu0 = u0z, cu1 = u1z, cH = Hz;
-                    } else if (cx == 0) {
-                        cu0 = u0r, cu1 = u1r, cH = Hr;
-                    } else if (cx == cy) {
-                        cu0 = padd(u0z, u0r), cu1 = padd(u1z, u1r), cH = padd(Hz, Hr);
-                    } else {
-                        cu0 = psub(u0z, u0r), cu1 = psub(u1z, u1r), cH = psub(Hz, Hr);
+                    T r = cy == 0 ? vz : (cx == 0 ? vr : (cx == cy ? padd(vz, vr) : psub(vz, vr)));
+                    if (cx + cy < 0) r = psub(pk(R(0), R(0)), r);  // the first direction points to -z or -r
+                    return r;
+                };
+                // link-midpoint source: this node's arrival half of the previous step's h_i and
+                // the departure half of this step's; this step's S0, H kept for the next step
+                const T half = pk(R(0.5), R(0.5));
+                const T hm0 = link ? pmul(half, m0) : m0, hHz = link ? pmul(half, Hz) : Hz;
+                const T hHr = link ? pmul(half, Hr) : Hr;
+                if (link) {
+                    fi[0] = pfma(pk(R(0.5) * w_of<R>(0), R(0.5) * w_of<R>(0)), ca[0], fi[0]);
+#pragma unroll
+                    for (int m = 0; m < 4; m++) {
+                        const int i = 2 * m + 1;
+                        const R w = w_of<R>(i);
+                        const T ea = pmul(pk(R(0.5) * w, R(0.5) * w), ca[0]);
+                        const T oa = pmul(pk(R(1.5) * w, R(1.5) * w), cdot(i, ca[1], ca[2]));
+                        fi[i] = padd(fi[i], padd(ea, oa));
+                        fi[i + 1] = padd(fi[i + 1], psub(ea, oa));
                     }
-                    if (cx + cy < 0) {  // the pair's first direction points to -z or -r: flip
-                        const T z = pk(R(0), R(0));
-                        cu0 = psub(z, cu0), cu1 = psub(z, cu1), cH = psub(z, cH);
+                    R* hq = hdst + row * pitch + k0 + cc;
+                    store_to(hq, 0, m0);
+                    store_to(hq, 1, Hz);
+                    store_to(hq, 2, Hr);
+                }
+                if (guo) {
+                    // Guo forcing: f*_i = f_i + omega (f^eq_i(u) - f_i) + S_i + h_i with
+                    // S_i = w_i (1 - omega/2) [3 (c_i - u).F + 9 (c_i.u)(c_i.F)], F = 2 rho (u - u0)
+                    const T r2 = pmul(pk(R(2), R(2)), rho);
+                    const T Fz = pmul(r2, psub(uz, u0z)), Fr = pmul(r2, psub(ur, u0r));
+                    const T usq = pfma(uz, uz, pmul(ur, ur)), uF = pfma(uz, Fz, pmul(ur, Fr));
+                    const R gpre = R(1) - R(0.5) * omega;
+                    const T om = pk(omega, omega), gp = pk(gpre, gpre);
+                    const T base = padd(pfma(om, psub(drho, pmul(c15, pmul(rho, usq))),
+                                             pmul(pk(R(-3) * gpre, R(-3) * gpre), uF)),
+                                        hm0);
+                    store(0, pfma(om1p, fi[0], pmul(pk(w_of<R>(0), w_of<R>(0)), base)));
+#pragma unroll
+                    for (int m = 0; m < 4; m++) {
+                        const int i = 2 * m + 1;
+                        const R w = w_of<R>(i);
+                        const T cu = cdot(i, uz, ur), cF = cdot(i, Fz, Fr), cH = cdot(i, hHz, hHr);
+                        const T even = pmul(pk(w, w), padd(base, padd(pmul(pk(R(4.5) * omega, R(4.5) * omega),
+                                                                           pmul(rho, pmul(cu, cu))),
+                                                                      pmul(pk(R(9) * gpre, R(9) * gpre), pmul(cu, cF)))));
+                        const T odd = pmul(pk(R(3) * w, R(3) * w), padd(padd(pmul(om, pmul(rho, cu)), pmul(gp, cF)), cH));
+                        store(i, padd(pfma(om1p, fi[i], even), odd));
+                        store(i + 1, psub(pfma(om1p, fi[i + 1], even), odd));
                     }
-                    const T even = pmul(pk(w, w), padd(padd(base, m0),
-                                                       pmul(rho, pmul(c45, psub(pmul(cu1, cu1),
-                                                                                pmul(om1p, pmul(cu0, cu0)))))));
-                    const T odd = pmul(pk(R(3) * w, R(3) * w), pfma(rho, psub(cu1, pmul(om1p, cu0)), cH));
-                    store(i, padd(pfma(om1p, fi[i], even), odd));
-                    store(i + 1, psub(pfma(om1p, fi[i + 1], even), odd));
+                } else {
+                    const T u0sq = pfma(u0z, u0z, pmul(u0r, u0r)), u1sq = pfma(u1z, u1z, pmul(u1r, u1r));
+                    const T base =
+                        pfma(pk(omega, omega), drho, pmul(rho, pmul(c15, psub(pmul(om1p, u0sq), u1sq))));
+                    store(0, pfma(om1p, fi[0], pmul(pk(w_of<R>(0), w_of<R>(0)), padd(base, hm0))));
+#pragma unroll
+                    for (int m = 0; m < 4; m++) {
+                        const int i = 2 * m + 1;  // i and i+1 are opposite
+                        const R w = w_of<R>(i);
+                        const T cu0 = cdot(i, u0z, u0r), cu1 = cdot(i, u1z, u1r), cH = cdot(i, hHz, hHr);
+                        const T even = pmul(pk(w, w), padd(padd(base, hm0),
+                                                           pmul(rho, pmul(c45, psub(pmul(cu1, cu1),
+                                                                                    pmul(om1p, pmul(cu0, cu0)))))));
+                        const T odd = pmul(pk(R(3) * w, R(3) * w), pfma(rho, psub(cu1, pmul(om1p, cu0)), cH));
+                        store(i, padd(pfma(om1p, fi[i], even), odd));
+                        store(i + 1, psub(pfma(om1p, fi[i + 1], even), odd));
+                    }
                 }
             }
         }
@@ -839,13 +989,14 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
 // (strip * nr + row) is cut into gridDim.x equal contiguous ranges; a CTA
 // marches each strip segment of its range (usually one or two).  rows_per_cta
 // > 0 instead gives fixed chunks: CTA (x, y) = strip x, rows [y R, y R + R).
-template <typename R, int TZ, int RR, int CP, bool MP, bool AX>
+template <typename R, int TZ, int RR, int CP, bool MP, bool AX, int FV = 0>
 __device__ __forceinline__ void march_cp(const Params<R>& p, const R* __restrict__ f, R* __restrict__ fout, int strip,
-                                         int j0, int jend, unsigned char* smem_raw, int& bad) {
+                                         int j0, int jend, unsigned char* smem_raw, int& bad,
+                                         const R* __restrict__ hsrc = nullptr, R* __restrict__ hdst = nullptr) {
     if constexpr (CP == 2)
-        march2<R, TZ, RR, MP, AX>(p, f, fout, strip, j0, jend, smem_raw, bad);
+        march2<R, TZ, RR, MP, AX, FV>(p, f, fout, strip, j0, jend, smem_raw, bad, hsrc, hdst);
     else
-        march<R, TZ, RR, MP, AX>(p, f, fout, strip, j0, jend, smem_raw, bad);
+        march<R, TZ, RR, MP, AX, FV>(p, f, fout, strip, j0, jend, smem_raw, bad, hsrc, hdst);
 }
 
 template <typename R, int TZ, int RR, int CP, int MINB, bool MP, bool AX>
@@ -878,8 +1029,9 @@ __global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB) k_step(Params
 // solve's (z-strip, row) space into tiles and deals them to the CTAs
 // (lbm_tiles.cu): CTA c marches tiles first[c] .. first[c + 1] - 1, each a row
 // range of one strip of one solve.  Even batch steps read f_a and write f_b,
-// odd steps the reverse.  A single solve runs as a batch of one.
-template <typename R, int TZ, int RR, int CP, int MINB, bool MP, bool AX>
+// odd steps the reverse (and the link source planes h_a / h_b likewise).  A
+// single solve runs as a batch of one.
+template <typename R, int TZ, int RR, int CP, int MINB, bool MP, bool AX, int FV = 0>
 __global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB)
     k_step_batch(const BatchSolve<R>* __restrict__ solves, const Tile* __restrict__ tiles,
                  const int* __restrict__ first, int parity, int* __restrict__ err) {
@@ -897,9 +1049,15 @@ __global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB)
         __syncthreads();  // parameters and the skip decision are the same for the whole CTA
         const R* fin = parity ? solves[tl.solve].f_b : solves[tl.solve].f_a;
         R* fo = parity ? const_cast<R*>(solves[tl.solve].f_a) : solves[tl.solve].f_b;
+        const R* hin = nullptr;
+        R* ho = nullptr;
+        if (FV & FV_LINK) {
+            hin = parity ? solves[tl.solve].h_b : solves[tl.solve].h_a;
+            ho = parity ? const_cast<R*>(solves[tl.solve].h_a) : solves[tl.solve].h_b;
+        }
         if (!skip) {
             int bad = 0;
-            march_cp<R, TZ, RR, CP, MP, AX>(sp, fin, fo, tl.strip, tl.j0, tl.jend, smem_raw, bad);
+            march_cp<R, TZ, RR, CP, MP, AX, FV>(sp, fin, fo, tl.strip, tl.j0, tl.jend, smem_raw, bad, hin, ho);
             if (bad) atomicOr(&err[tl.solve], bad);
         }
     }

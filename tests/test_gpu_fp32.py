@@ -231,21 +231,27 @@ def test_maximum_grid_sampled_windows():
         assert vel_err(g, r) <= 1e-4
 
 
-def test_link_midpoint_source_fp32():
-    """h_eval = LINK_AVG on the two-kernel path in FP32 (rho_ref = rho_v)
-    against the oracle's link average, droplet from rest with a random flow,
-    300 steps: the droplet bars."""
-    c = Case(64, 48, h_eval=O.H_LINK_AVG)
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("forcing,h_eval", [(O.FORCING_EDM, O.H_LINK_AVG), (O.FORCING_GUO, O.H_LOCAL)])
+def test_collision_forms_fp32(forcing, h_eval, path):
+    """h_eval = LINK_AVG and Guo forcing in FP32 (rho_ref = rho_v), through the
+    fused kernel's forms (path 1) and the two-kernel path (2), against the
+    oracle: droplet from rest with a random flow, 300 steps, the droplet bars."""
+    from paper_1512_01977_gb300 import lbm
+
+    c = Case(64, 48, h_eval=h_eval, forcing=forcing)
     rv, rl = c.coexistence()
     rho, _, _ = I.droplet(64, 48, 14, rl, rv)
     _, vz, vr = I.random_state(64, 48, 1.0, 0.0, 2e-3, 44)
     fields = (rho, vz, vr * (np.arange(48) + 0.5)[:, None] / 48)
     o = O.Oracle(c.oracle_params()).init(*fields, physical=True).step(300)
-    s = c.solver(32, rv).init(*fields, physical=True).step(300)
+    s = c.solver(32, rv).init(*fields, physical=True)
+    lbm.lbm_axi_set_tuning(s.h, path, 0)
+    s.step(300)
     mo, mg = o.moments(), s.moments()
     mr, _ = s.mass()
     s.close()
     e = {"rho": rel_err(mg["rho"], mo["rho"]), "u": vel_err(mg, mo), "p": rel_err(mg["p"], mo["p"]),
          "mass": abs(mr / o.mass_rweighted() - 1)}
-    print("FP32 link-midpoint errors", e)
+    print("FP32 forcing %d h_eval %d path %d errors" % (forcing, h_eval, path), e)
     assert e["rho"] <= 2e-4 and e["u"] <= 1e-3 and e["p"] <= 1e-3 and e["mass"] <= 2e-5, e

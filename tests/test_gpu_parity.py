@@ -99,27 +99,65 @@ def test_fp64_wide_grid_balanced_and_chunked(rows_per_cta):
     _compare(c, (rho, vz, vr * (np.arange(37) + 0.5)[:, None] / 37), 70, tuning=(lbm.PATH_FUSED, rows_per_cta))
 
 
+@pytest.mark.parametrize("path", ["fused", "split"])
 @pytest.mark.parametrize("top", [O.TOP_FREESLIP, O.TOP_NOSLIP])
-def test_guo_forcing_fp64(top):
-    """Guo forcing (two-kernel path) against the oracle: a droplet started at
-    rest with a random flow, and a single-phase channel driven by a body force."""
+def test_guo_forcing_fp64(top, path):
+    """Guo forcing against the oracle, through the fused kernel's Guo form (the
+    default with the force and the axis terms on) and the two-kernel path: a
+    droplet started at rest with a random flow, and a single-phase channel driven
+    by a body force (two-kernel path: the fused forms need the force on)."""
     from paper_1512_01977_gb300 import lbm
 
     c = Case(45, 27, top=top, forcing=O.FORCING_GUO)
     fields = _droplet_fields(c, 10, du=2e-3, seed=41)
     o = O.Oracle(c.oracle_params()).init(*fields, physical=True).step(80)
     s = c.solver().init(*fields, physical=True)
-    assert lbm.lbm_axi_get_tuning(s.h)[0] == lbm.PATH_SPLIT
+    assert lbm.lbm_axi_get_tuning(s.h)[0] == lbm.PATH_FUSED
     with pytest.raises(lbm.LbmError):
-        lbm.lbm_axi_set_tuning(s.h, lbm.PATH_FUSED, 0)
+        lbm.lbm_axi_set_tuning(s.h, lbm.PATH_FUSED, 16)  # chunked grids have the EDM form only
     with pytest.raises(lbm.LbmError):
         lbm.Batch([s])
+    if path == "split":
+        lbm.lbm_axi_set_tuning(s.h, lbm.PATH_SPLIT, 0)
     s.step(80)
     mg = s.moments()
     s.close()
     _check(mg, o.moments())
     c = Case(8, 16, multiphase=0, top=O.TOP_NOSLIP, gz=1e-5, forcing=O.FORCING_GUO)
+    s = c.solver()
+    assert lbm.lbm_axi_get_tuning(s.h)[0] == lbm.PATH_SPLIT
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_axi_set_tuning(s.h, lbm.PATH_FUSED, 0)
+    s.close()
     _compare(c, I.random_state(8, 16, 1.0, 0.01, 1e-3, 6), 200)
+
+
+@pytest.mark.parametrize("top", [O.TOP_FREESLIP, O.TOP_NOSLIP])
+@pytest.mark.parametrize("forcing,h_eval", [(O.FORCING_GUO, O.H_LOCAL), (O.FORCING_EDM, O.H_LINK_AVG),
+                                            (O.FORCING_GUO, O.H_LINK_AVG)])
+def test_collision_forms_wide_grid_fp64(forcing, h_eval, top):
+    """The fused kernel's Guo and link-source forms on a 230 x 33 grid (three
+    z-strips, a ragged last one; a droplet pair, one across the periodic z seam)
+    against the oracle, with both wall tops."""
+    from paper_1512_01977_gb300 import lbm
+
+    nz, nr = 230, 33
+    c = Case(nz, nr, top=top, forcing=forcing, h_eval=h_eval)
+    s = c.solver()
+    assert lbm.lbm_axi_get_tuning(s.h)[0] == lbm.PATH_FUSED
+    s.close()
+    rv, rl = c.coexistence()
+    rho, _, _ = I.droplet(nz, nr, 10, rl, rv)
+    rho = np.maximum(rho, np.roll(rho, nz // 2 + 1, axis=1))
+    _, vz, vr = I.random_state(nz, nr, 1.0, 0.0, 2e-3, 77)
+    ur = vr * (np.arange(nr) + 0.5)[:, None] / nr
+    # the given velocity is the physical one (with EDM and the link source a start
+    # at u0 = u leaves the coexistence state within ~15 steps, in the oracle too)
+    o = O.Oracle(c.oracle_params()).init(rho, vz, ur, physical=True).step(60)
+    s = c.solver().init(rho, vz, ur, physical=True).step(60)
+    mg = s.moments()
+    s.close()
+    _check(mg, o.moments())
 
 
 def test_init_moments_roundtrip():
@@ -398,10 +436,12 @@ def test_checkpoint_resume_is_exact(precision):
     b.close()
 
 
+@pytest.mark.parametrize("path", ["fused", "split"])
 @pytest.mark.parametrize("top", [O.TOP_FREESLIP, O.TOP_NOSLIP])
-def test_link_midpoint_source_fp64(top):
-    """h_eval = LINK_AVG (two-kernel path) against the oracle's link average:
-    a droplet from rest with a random flow, and the radial acoustic mode."""
+def test_link_midpoint_source_fp64(top, path):
+    """h_eval = LINK_AVG against the oracle's link average, through the fused
+    kernel's link form and the two-kernel path: a droplet from rest with a
+    random flow, and the radial acoustic mode (single phase: two-kernel path)."""
     from scipy import special
 
     c = Case(45, 27, top=top, h_eval=O.H_LINK_AVG)
@@ -410,7 +450,9 @@ def test_link_midpoint_source_fp64(top):
     s = c.solver().init(*fields, physical=True)
     from paper_1512_01977_gb300 import lbm
 
-    assert lbm.lbm_axi_get_tuning(s.h)[0] == lbm.PATH_SPLIT
+    assert lbm.lbm_axi_get_tuning(s.h)[0] == lbm.PATH_FUSED
+    if path == "split":
+        lbm.lbm_axi_set_tuning(s.h, lbm.PATH_SPLIT, 0)
     s.step(90)
     mo, mg = o.moments(), s.moments()
     assert rel_err(mg["rho"], mo["rho"]) <= TOL64 and vel_err(mg, mo) <= TOL64 and rel_err(mg["p"], mo["p"]) <= TOL64
@@ -421,7 +463,7 @@ def test_link_midpoint_source_fp64(top):
 
 
 def test_link_midpoint_source_limits():
-    """A LINK_AVG solve refuses the fused path and batches; its checkpoint
+    """A LINK_AVG solve refuses chunked fused grids and batches; its checkpoint
     carries the source planes (bitwise resume)."""
     from paper_1512_01977_gb300 import lbm
 
@@ -429,7 +471,7 @@ def test_link_midpoint_source_limits():
     fields = _droplet_fields(c, 9, du=1e-3, seed=32)
     s = c.solver(32, c.coexistence()[0]).init(*fields, physical=True)
     with pytest.raises(lbm.LbmError):
-        lbm.lbm_axi_set_tuning(s.h, lbm.PATH_FUSED, 0)
+        lbm.lbm_axi_set_tuning(s.h, lbm.PATH_FUSED, 16)
     with pytest.raises(lbm.LbmError):
         lbm.Batch([s])
     s.step(11)
