@@ -118,7 +118,7 @@ def _source_hash():
 def _ncu_traffic():
     """Per-launch DRAM bytes of the fused step kernel on this workload from the
     committed ncu summary, or None when the kernel sources changed since."""
-    path = os.path.join(ROOT, "profiles", "k_step_batch_fp32_wave4096x2048.md")
+    path = os.path.join(ROOT, "profiles", "k_step_single_fp32_wave4096x2048.md")
     try:
         vals = {}
         with open(path) as fh:
@@ -436,7 +436,7 @@ def run_ours(args):
                        "parallelism": "replicas only (independent solves per GPU)",
                        "device": props.name},
             "roofline": {"bound": "hbm",
-                         "kernel": "k_step_batch (one-pass gather+psi+forces+EDM+source+collide; a batch of one)"
+                         "kernel": "k_step_single (one-pass gather+psi+forces+EDM+source+collide; the single-solve form)"
                          if path == lbm.PATH_FUSED else "k_update (forces+EDM+source+collide)",
                          "achieved": ach_b, "peak": peak, "unit": "GB/s", "frac": ach_b / peak,
                          "peak_source": peak_kind, "traffic": traffic,

@@ -39,15 +39,18 @@ int pitch_of(int nz) { return (nz + 31) / 32 * 32; }
 
 #include "lbm_handle.h"
 
-// The balanced one-wave grid: the batched kernel with a batch of one, so a
-// solve runs the same code alone as inside any batch.
+// The balanced one-wave grid: the fused kernel over this solve's tile plan, its
+// descriptor passed by value; the same arithmetic as inside any batch.
 cudaError_t lbm_handle_step_tiles(lbm_axi* h, int c) {
     const bool mp = h->opts.multiphase != 0, ax = h->opts.axis_terms != 0;
-    if (h->precision == 32)
-        return Ops<float>::step_batch(static_cast<const lbm::BatchSolve<float>*>(h->d_self), h->d_tiles, h->d_first,
-                                      h->ncta, mp, ax, c, lbm::kStripWide, h->derr, h->stream, fv_of(h));
-    return Ops<double>::step_batch(static_cast<const lbm::BatchSolve<double>*>(h->d_self), h->d_tiles, h->d_first,
-                                   h->ncta, mp, ax, c, lbm::kStripWide, h->derr, h->stream, fv_of(h));
+    if (h->precision == 32) {
+        const lbm::BatchSolve<float> d{h->pf, (const float*)h->f[0], (float*)h->f[1], (const float*)h->hb[0],
+                                       (float*)h->hb[1]};
+        return Ops<float>::step_single(d, h->d_tiles, h->d_first, h->ncta, mp, ax, c, h->derr, h->stream, fv_of(h));
+    }
+    const lbm::BatchSolve<double> d{h->pdd, (const double*)h->f[0], (double*)h->f[1], (const double*)h->hb[0],
+                                    (double*)h->hb[1]};
+    return Ops<double>::step_single(d, h->d_tiles, h->d_first, h->ncta, mp, ax, c, h->derr, h->stream, fv_of(h));
 }
 
 namespace {
@@ -215,7 +218,6 @@ void release_all(lbm_axi* h) {
     dev_free(h->partial, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->dred, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->derr, h->via_hook, h->hook_ctx, h->hook_release);
-    dev_free(h->d_self, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->d_tiles, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->d_first, h->via_hook, h->hook_ctx, h->hook_release);
     dev_free(h->hb[0], h->via_hook, h->hook_ctx, h->hook_release);
@@ -315,8 +317,7 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     h->partial = (double*)dev_alloc(4 * lbm::kReduceBlocks * sizeof(double));
     h->dred = (double*)dev_alloc(4 * sizeof(double));
     h->derr = (int*)dev_alloc(sizeof(int));
-    h->d_self = dev_alloc(o.precision == 32 ? sizeof(lbm::BatchSolve<float>) : sizeof(lbm::BatchSolve<double>));
-    // tile plan of the balanced one-wave step (the batched kernel with a batch of one)
+    // tile plan of the balanced one-wave step (k_step_single, the batched kernel's single-solve form)
     std::vector<lbm::Tile> tiles;
     std::vector<int> first;
     {
@@ -345,7 +346,7 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
         h->hb[1] = dev_alloc(3 * plane_bytes);
         h->bytes += 6 * plane_bytes;
     }
-    bool ok = h->f[0] && h->f[1] && h->aux && h->mout && h->partial && h->dred && h->derr && h->d_self &&
+    bool ok = h->f[0] && h->f[1] && h->aux && h->mout && h->partial && h->dred && h->derr &&
               h->d_tiles && h->d_first && (!link || (h->hb[0] && h->hb[1]));
     ok = ok && cudaMallocHost(&h->herr, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMallocHost(&h->hred, 4 * sizeof(double)) == cudaSuccess;
@@ -374,18 +375,8 @@ int lbm_axi_create(int nz, int nr, double tau, const lbm_eos* eos, double A, con
     *h->herr = 0;
     cudaError_t err = cudaSuccess;
     {
-        // descriptor of this solve for the batched kernel (wide strips) and its tile plan
-        if (o.precision == 32) {
-            lbm::BatchSolve<float> d{h->pf, (const float*)h->f[0], (float*)h->f[1], (const float*)h->hb[0],
-                                     (float*)h->hb[1]};
-            err = cudaMemcpy(h->d_self, &d, sizeof(d), cudaMemcpyHostToDevice);
-        } else {
-            lbm::BatchSolve<double> d{h->pdd, (const double*)h->f[0], (double*)h->f[1], (const double*)h->hb[0],
-                                      (double*)h->hb[1]};
-            err = cudaMemcpy(h->d_self, &d, sizeof(d), cudaMemcpyHostToDevice);
-        }
-        if (err == cudaSuccess)
-            err = cudaMemcpy(h->d_tiles, tiles.data(), tiles.size() * sizeof(lbm::Tile), cudaMemcpyHostToDevice);
+        // this solve's tile plan (wide strips, one resident wave)
+        err = cudaMemcpy(h->d_tiles, tiles.data(), tiles.size() * sizeof(lbm::Tile), cudaMemcpyHostToDevice);
         if (err == cudaSuccess)
             err = cudaMemcpy(h->d_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice);
     }

@@ -429,7 +429,7 @@ int lbm_axi_autotune(lbm_axi* h, int trials, lbm_axi_tuning* chosen) {
         return e;
     };
     if (fused_ok(h)) {
-        // rows 0: the balanced wave (a batch of one, the form every collision variant has)
+        // rows 0: the balanced wave over the tile plan (the form every collision variant has)
         const int rows_list[5] = {0, 32, 64, 144, 256};
         const int nrows = fv_of(h) ? 1 : 5;
         for (int q = 0; q < nrows; q++) {

@@ -39,9 +39,8 @@ struct lbm_axi {
     int pending;  // error status carried to the next sync
     size_t bytes;
     int path;          // LBM_PATH_FUSED or LBM_PATH_SPLIT
-    int rows_per_cta;  // fused path: 0 = balanced wave (the batched kernel, batch of one); > 0 = chunks
+    int rows_per_cta;  // fused path: 0 = balanced wave (k_step_single over the tile plan); > 0 = chunks
                        // (EDM with h_i at the node only)
-    void* d_self;       // BatchSolve<R> of this solve (f_a = f[0], f_b = f[1], h_a = hb[0], h_b = hb[1])
     lbm::Tile* d_tiles;  // tile plan of this solve alone (wide strips, one resident wave)
     int* d_first;        // [ncta + 1]
     int ncta;
@@ -70,7 +69,7 @@ inline bool fused_ok(const lbm_axi* h) {
 // Options the batched engine lacks (such a solve cannot join a batch).
 inline bool unbatchable(const lbm_axi* h) { return fv_of(h) != 0; }
 
-// One fused step of this solve as a batch of one (its tile plan, the collision
+// One fused step of this solve over its tile plan (k_step_single, the collision
 // form fv_of(h)) reading f[c] and writing f[c^1]; enqueued on h->stream.
 cudaError_t lbm_handle_step_tiles(lbm_axi* h, int c);
 

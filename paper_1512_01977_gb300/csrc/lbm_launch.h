@@ -54,6 +54,10 @@ struct Ops {
     // kStripWide and mp && ax (cudaErrorInvalidValue otherwise).
     static cudaError_t step_batch(const BatchSolve<R>* solves, const Tile* tiles, const int* first, int ncta,
                                   bool mp, bool ax, int parity, int strip, int* err, cudaStream_t s, int fv = 0);
+    // The fused step of one solve, descriptor by value (kStripWide tiles; same
+    // arithmetic as step_batch with a batch of one).
+    static cudaError_t step_single(const BatchSolve<R>& solve, const Tile* tiles, const int* first, int ncta,
+                                   bool mp, bool ax, int parity, int* err, cudaStream_t s, int fv = 0);
     static int batch_resident_ctas(int strip);
     static size_t batch_smem(int strip);
 };

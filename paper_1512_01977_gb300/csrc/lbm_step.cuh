@@ -1063,4 +1063,36 @@ __global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB)
     }
 }
 
+// The same step for a single solve, its descriptor passed by value: the
+// parameters are read from the kernel's constant bank instead of a shared-memory
+// copy per tile (fewer shared-memory loads on the bound pipe; the arithmetic,
+// and so every result, is that of k_step_batch for a batch of one).
+template <typename R, int TZ, int RR, int CP, int MINB, bool MP, bool AX, int FV = 0>
+__global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB)
+    k_step_single(const BatchSolve<R> s, const Tile* __restrict__ tiles, const int* __restrict__ first, int parity,
+                  int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int skip;  // the solve already went unphysical: its populations are void, leave them
+    const R* fin = parity ? s.f_b : s.f_a;
+    R* fo = parity ? const_cast<R*>(s.f_a) : s.f_b;
+    const R* hin = nullptr;
+    R* ho = nullptr;
+    if (FV & FV_LINK) {
+        hin = parity ? s.h_b : s.h_a;
+        ho = parity ? const_cast<R*>(s.h_a) : s.h_b;
+    }
+    const int t1 = first[blockIdx.x + 1];
+    for (int t = first[blockIdx.x]; t < t1; t++) {
+        const Tile tl = tiles[t];
+        __syncthreads();  // everyone is done with the previous tile
+        if (threadIdx.x == 0) skip = *static_cast<volatile const int*>(err);
+        __syncthreads();
+        if (!skip) {
+            int bad = 0;
+            march_cp<R, TZ, RR, CP, MP, AX, FV>(s.p, fin, fo, tl.strip, tl.j0, tl.jend, smem_raw, bad, hin, ho);
+            if (bad) atomicOr(err, bad);
+        }
+    }
+}
+
 }  // namespace lbm

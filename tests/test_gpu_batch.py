@@ -43,7 +43,7 @@ def _mix(seed=4, n=7, precision=64):
 @pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("strip", [64, 112])
 def test_batch_equals_alone(lbm, precision, strip):
-    """Same kernel code alone (a batch of one, strip 112) and in the batch:
+    """Same arithmetic alone (the single-solve form, strip 112) and in the batch:
     bitwise equal at strip 112; with strip 64 (another compiled form) FP32
     may differ in the last bits (FMA contraction), bounded here by 1e-6."""
     mix = _mix(precision=precision)

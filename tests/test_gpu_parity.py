@@ -88,7 +88,7 @@ def test_fp64_grids_wider_than_a_strip(nz, nr, top):
 @pytest.mark.parametrize("rows_per_cta", [0, 16])
 def test_fp64_wide_grid_balanced_and_chunked(rows_per_cta):
     """A 290 x 37 droplet pair through the balanced one-wave grid (the batched
-    kernel, a batch of one) and through 16-row chunks of the single-solve kernel."""
+    kernel's single-solve form) and through 16-row chunks of the chunked kernel."""
     c = Case(290, 37)
     rv, rl = c.coexistence()
     rho, _, _ = I.droplet(290, 37, 11, rl, rv)
