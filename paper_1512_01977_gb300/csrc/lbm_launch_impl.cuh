@@ -12,9 +12,9 @@ template <typename R>
 struct UpdateTile;
 template <>
 struct UpdateTile<float> {
-    // 32 x 32: 540 us per launch on the 4096 x 2048 wave against 572 us for 32 x 16
-    // (less halo work); wider or taller tiles lose occupancy (64 x 16: 681 us)
-    static constexpr int TZ = 32, TR = 32;
+    // 32 x 16: through the C ABI on the 2048 x 2048 wave 235 us per launch against
+    // 263 us for 32 x 32; wider tiles lose occupancy
+    static constexpr int TZ = 32, TR = 16;
 };
 template <>
 struct UpdateTile<double> {
