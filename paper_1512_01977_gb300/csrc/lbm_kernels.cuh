@@ -112,11 +112,11 @@ struct TileShape {
     static constexpr int elems = PW * PH + 2 * DW * DH + 5 * UW * UH + 2 * TZ * TR;
 };
 
-// guo != 0: Guo forcing (Sec. II.A) in place of the EDM shift (only this kernel has it).
-template <typename R, int TZ, int TR, bool MOMENTS>
+// GUO: Guo forcing (Sec. II.A) in place of the EDM shift.
+template <typename R, int TZ, int TR, bool MOMENTS, bool GUO = false>
 __global__ void __launch_bounds__(256) k_update(Params<R> p, Params<double> pd, const R* __restrict__ f,
                                                 R* __restrict__ fout, const R* __restrict__ aux,
-                                                double* __restrict__ mout, LinkPlanes<R> lk, int guo) {
+                                                double* __restrict__ mout, LinkPlanes<R> lk) {
     using S = TileShape<TZ, TR>;
     constexpr int PW = S::PW, PH = S::PH, DW = S::DW, DH = S::DH, UW = S::UW, UH = S::UH;
     constexpr int NT = 256;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(256) k_update(Params<R> p, Params<double> pd, 
             R fi = f[pull_slot(p, k, j, i)];
             if (lk.src) fi += R(0.5) * w * (a0 + R(3) * (cx * az + cy * ar));
             R feq, force;
-            if (guo) {
+            if (GUO) {
                 const R cu = cx * uz + cy * ur, cF = cx * Fz + cy * Fr;
                 feq = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq));
                 force = w * gpre * (R(3) * (cF - uF) + R(9) * cu * cF);

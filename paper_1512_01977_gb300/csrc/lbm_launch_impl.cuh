@@ -12,9 +12,9 @@ template <typename R>
 struct UpdateTile;
 template <>
 struct UpdateTile<float> {
-    // 32 x 16: through the C ABI on the 2048 x 2048 wave 235 us per launch against
-    // 263 us for 32 x 32; wider tiles lose occupancy
-    static constexpr int TZ = 32, TR = 16;
+    // 32 x 32: 512 us per launch through the C ABI on the 4096 x 2048 wave against
+    // 559 us for 32 x 16 (less halo work); wider tiles lose occupancy (64 x 16: +19 %)
+    static constexpr int TZ = 32, TR = 32;
 };
 template <>
 struct UpdateTile<double> {
@@ -34,9 +34,11 @@ static cudaError_t launch_update(const Params<R>& p, const Params<double>& pd, c
     const size_t smem = Ops<R>::update_smem();
     dim3 grid((p.nz + T::TZ - 1) / T::TZ, (p.nr + T::TR - 1) / T::TR);
     if (moments) {
-        k_update<R, T::TZ, T::TR, true><<<grid, 256, smem, s>>>(p, pd, f, nullptr, aux, mout, lk, 0);
+        k_update<R, T::TZ, T::TR, true><<<grid, 256, smem, s>>>(p, pd, f, nullptr, aux, mout, lk);
+    } else if (guo) {
+        k_update<R, T::TZ, T::TR, false, true><<<grid, 256, smem, s>>>(p, pd, f, fout, aux, nullptr, lk);
     } else {
-        k_update<R, T::TZ, T::TR, false><<<grid, 256, smem, s>>>(p, pd, f, fout, aux, nullptr, lk, guo ? 1 : 0);
+        k_update<R, T::TZ, T::TR, false><<<grid, 256, smem, s>>>(p, pd, f, fout, aux, nullptr, lk);
     }
     return cudaGetLastError();
 }
@@ -94,6 +96,9 @@ cudaError_t Ops<R>::prepare() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_update<R, T::TZ, T::TR, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_update<R, T::TZ, T::TR, false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = set_step_attr<R>((int)step_smem());
     // the batched kernel (also the default single-solve step): attributes and
     // occupancy are settled here, outside any stream capture
