@@ -28,8 +28,9 @@ typedef struct {
 } lbm_axi_batch_tuning;
 
 /* Group n >= 1 solves.  Every solve must be created on the current device,
- * initialised, on the fused path (nr >= 16), with the same precision and the
- * same multiphase / axis_terms switches; a solve may appear once.  The batch
+ * initialised, with nr >= 16, EDM forcing and h_i at the node (the batched
+ * kernel has neither the Guo nor the link-source form), the same precision and
+ * the same multiphase / axis_terms switches; a solve may appear once.  The batch
  * borrows the solves: while it exists they must not be stepped, initialised or
  * destroyed through their own handles; their moments and mass may be read
  * after lbm_axi_batch_sync.  stream: a cudaStream_t for the batch's work, or
