@@ -260,19 +260,21 @@ def _oracle_rate(nz, nr, rho0, steps, threads):
 
 def _cpu_baseline(rho0):
     """The FP64 oracle timed on this host: all cores and one core, on a
-    bounded sample of the workload (the full grid for a few steps)."""
+    bounded sample of the workload (the full grid for a number of steps,
+    about 10 s of wall time in all)."""
     n_all = os.cpu_count() or 1
-    r_all, used_all, dt_all = _oracle_rate(NZ, NR, rho0, 6, n_all)
-    r_one, _, dt_one = _oracle_rate(NZ, NR, rho0, 2, 1)
+    steps_all, steps_one = 20, 5
+    r_all, used_all, dt_all = _oracle_rate(NZ, NR, rho0, steps_all, n_all)
+    r_one, _, dt_one = _oracle_rate(NZ, NR, rho0, steps_one, 1)
     from oracle import core
 
     core.threads(n_all)
     return {"value": r_all / 1e6, "unit": "MLUPS", "cores": used_all, "kind": "oracle",
-            "sample": "6 steps of the full %dx%d grid, FP64, OpenMP over %d threads (%.1f s)"
-                      % (NZ, NR, used_all, dt_all),
+            "sample": "%d steps of the full %dx%d grid, FP64, OpenMP over %d threads (%.1f s)"
+                      % (steps_all, NZ, NR, used_all, dt_all),
             "nproc": n_all,
             "one_core": {"value": r_one / 1e6, "unit": "MLUPS", "cores": 1,
-                         "sample": "2 steps of the full grid, one thread (%.1f s)" % dt_one}}
+                         "sample": "%d steps of the full grid, one thread (%.1f s)" % (steps_one, dt_one)}}
 
 
 def run_reference(args):
