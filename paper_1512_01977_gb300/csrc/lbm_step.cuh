@@ -678,17 +678,34 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
     // Items: (row offset, first column of the pair); inactive items get a row
     // offset far out of range.  Lane 1 of a pair may lie past the strip's
     // last used column: it is computed (from in-range data) but never stored
-    // to global memory and raises no error bits.
+    // to global memory and raises no error bits.  With 128 threads and rows of
+    // at most 64 pairs (112-column strips) each row's items sit on two whole
+    // warps: no warp straddles two ring rows, whose loads would replay as bank
+    // conflicts (a reader stage's row is narrower than the ring's stride);
+    // measured 2 % faster.  Otherwise the items of a stage are packed row after row.
     constexpr int OFF = -100000;
-    const int lr = tid / HL, lc = 2 * (tid - (tid / HL) * HL);
-    const int l_rr = (tid < RR * HL && lc < kn + 12) ? lr : OFF;
+    constexpr bool kWarpRows = S::NT == 128 && RR == 2 && HL <= 64;
+    int lr, lc, dr_, dc, ur_, uc, cr_, cc;
+    bool la, da, ua, ca;
+    if (kWarpRows) {
+        const int wrow = tid >> 6, wcol = tid & 63;
+        lr = dr_ = ur_ = cr_ = wrow;
+        lc = dc = uc = cc = 2 * wcol;
+        la = wcol < HL;
+        da = wcol < HD;
+        ua = wcol < HU;
+        ca = wcol < HC;
+    } else {
+        lr = tid / HL, lc = 2 * (tid - (tid / HL) * HL), la = tid < RR * HL;
+        dr_ = tid / HD, dc = 2 * (tid - (tid / HD) * HD), da = tid < RR * HD;
+        ur_ = tid / HU, uc = 2 * (tid - (tid / HU) * HU), ua = tid < RR * HU;
+        cr_ = tid / HC, cc = 2 * (tid - (tid / HC) * HC), ca = tid < RR * HC;
+    }
+    const int l_rr = (la && lc < kn + 12) ? lr : OFF;
     const bool l_v1 = lc + 1 < kn + 12;
-    const int dr_ = tid / HD, dc = 2 * (tid - (tid / HD) * HD);
-    const int d_rr = (tid < RR * HD && dc < kn + 8) ? dr_ : OFF;
-    const int ur_ = tid / HU, uc = 2 * (tid - (tid / HU) * HU);
-    const int u_rr = (tid < RR * HU && uc < kn + 4) ? ur_ : OFF;
-    const int cr_ = tid / HC, cc = 2 * (tid - (tid / HC) * HC);
-    const int c_rr = (tid < RR * HC && cc < kn) ? cr_ : OFF;
+    const int d_rr = (da && dc < kn + 8) ? dr_ : OFF;
+    const int u_rr = (ua && uc < kn + 4) ? ur_ : OFF;
+    const int c_rr = (ca && cc < kn) ? cr_ : OFF;
     const bool c_v1 = cc + 1 < kn;
 
     const int lk = wrap_any(k0 - 6 + lc, nz);
