@@ -49,7 +49,7 @@ struct StepTile;
 // CP: columns per thread (2: march2, pairs of nodes with packed FP32 arithmetic).
 template <>
 struct StepTile<float> {
-    static constexpr int TZ = 112, RR = 2, CP = 2, MINB = 4;  // 128 threads, 48 KB of rings (rows padded)
+    static constexpr int TZ = 112, RR = 2, CP = 2, MINB = 4;  // 128 threads, 45.3 KB of rings
 };
 template <>
 struct StepTile<double> {
@@ -58,7 +58,7 @@ struct StepTile<double> {
 
 template <typename R>
 size_t Ops<R>::step_smem() {
-    return sizeof(R) * (size_t)StepShape<StepTile<R>::TZ, StepTile<R>::RR, StepTile<R>::CP>::elems;
+    return sizeof(R) * (size_t)StepShape<StepTile<R>::TZ, StepTile<R>::RR>::elems;
 }
 
 template <typename R>
@@ -202,7 +202,7 @@ namespace lbm {
 // Batched kernel forms: strip width kStripNarrow or kStripWide (the autotuner picks), force and
 // axis terms compiled in or out.
 // Resident CTAs per SM the launch bounds ask for: what shared memory allows at
-// each width (FP32 two columns per thread: 48 KB / 26.9 KB of rings; FP64
+// each width (FP32 two columns per thread: 45.3 KB / 26.9 KB of rings; FP64
 // one column: 90.6 KB / 53.8 KB).
 template <typename R, int TZ>
 struct BatchMinBlocks {

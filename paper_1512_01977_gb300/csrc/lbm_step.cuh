@@ -115,15 +115,7 @@ struct StepShape {
     static constexpr int NT = (RR * WL / CP + 31) / 32 * 32;
     // ring depths (rows), powers of two; schedule checked on the CPU for RR = 2 and 4
     static constexpr int DP = RR <= 2 ? 16 : 32, DD = RR <= 2 ? 8 : 16, DJ = RR <= 2 ? 16 : 32, DU = RR <= 2 ? 8 : 16;
-    // Two columns per thread, 128 threads, 2 rows of at most 64 pairs: each row's
-    // items sit on two whole warps (march2), and ring rows are padded to 32
-    // elements (128 B in FP32) so every warp's row segment has the same bank
-    // alignment (measured 0.7 % faster).  Otherwise the stride is the width.
-    static constexpr bool WROWS = CP == 2 && NT == 128 && RR == 2 && WL / 2 <= 64;
-    static constexpr int SL = WROWS ? (WL + 31) / 32 * 32 : WL;
-    static constexpr int SD = WROWS ? (WD + 31) / 32 * 32 : WD;
-    static constexpr int SU = WROWS ? (WU + 31) / 32 * 32 : WU;
-    static constexpr int elems = DP * SL + 2 * DD * SD + 3 * DJ * SU + 2 * DU * SU;
+    static constexpr int elems = DP * WL + 2 * DD * WD + 3 * DJ * WU + 2 * DU * WU;
     // schedule constraints
     static_assert(11 + 2 * RR <= DP && 4 + 2 * RR <= DD && 6 + 4 * RR <= DJ && 4 + 2 * RR <= DU, "ring depth");
 };
@@ -662,15 +654,14 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
     constexpr int WL = S::WL, WD = S::WD, WU = S::WU, LAG = S::LAG;
     constexpr int DP = S::DP, DD = S::DD, DJ = S::DJ, DU = S::DU;
     constexpr int HL = WL / 2, HD = WD / 2, HU = WU / 2, HC = TZ / 2;  // pairs per row
-    constexpr int SL = S::SL, SD = S::SD, SU = S::SU;  // ring row strides
-    R* sPsi = reinterpret_cast<R*>(smem_raw);  // [DP][SL]
-    R* sPz = sPsi + DP * SL;                   // [DD][SD]
-    R* sPr = sPz + DD * SD;
-    R* sRho = sPr + DD * SD;  // [DJ][SU]  rho - rho_ref
-    R* sJz = sRho + DJ * SU;
-    R* sJr = sJz + DJ * SU;
-    R* sUz = sJr + DJ * SU;  // [DU][SU]  physical velocity
-    R* sUr = sUz + DU * SU;
+    R* sPsi = reinterpret_cast<R*>(smem_raw);  // [DP][WL]
+    R* sPz = sPsi + DP * WL;                   // [DD][WD]
+    R* sPr = sPz + DD * WD;
+    R* sRho = sPr + DD * WD;  // [DJ][WU]  rho - rho_ref
+    R* sJz = sRho + DJ * WU;
+    R* sJr = sJz + DJ * WU;
+    R* sUz = sJr + DJ * WU;  // [DU][WU]  physical velocity
+    R* sUr = sUz + DU * WU;
 
     const int tid = threadIdx.x;
     const int k0 = strip * TZ;
@@ -693,7 +684,7 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
     // conflicts (a reader stage's row is narrower than the ring's stride);
     // measured 2 % faster.  Otherwise the items of a stage are packed row after row.
     constexpr int OFF = -100000;
-    constexpr bool kWarpRows = S::WROWS;
+    constexpr bool kWarpRows = S::NT == 128 && RR == 2 && HL <= 64;
     int lr, lc, dr_, dc, ur_, uc, cr_, cc;
     bool la, da, ua, ca;
     if (kWarpRows) {
@@ -780,12 +771,12 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
                 if (mp) {
                     const T arg = psub(pmul(rho, pk(R(1) / R(3), R(1) / R(3))), eos_p2<R>(p, rho));
                     if (!(arg.x >= R(0)) || (l_v1 && !(arg.y >= R(0)))) bad |= ERRBIT_PSI;
-                    st2(sPsi + (row & (DP - 1)) * SL, lc, pk(sqrt_nonneg(arg.x), sqrt_nonneg(arg.y)));
+                    st2(sPsi + (row & (DP - 1)) * WL, lc, pk(sqrt_nonneg(arg.x), sqrt_nonneg(arg.y)));
                 }
                 if (!(rho.x > R(0)) || (l_v1 && !(rho.y > R(0)))) bad |= ERRBIT_RHO;
                 const int cu = lc - 4;
                 if (cu >= 0 && cu < WU) {
-                    const int sj = (row & (DJ - 1)) * SU;
+                    const int sj = (row & (DJ - 1)) * WU;
                     st2(sRho + sj, cu, drho);
                     st2(sJz + sj, cu, jz);
                     st2(sJr + sj, cu, (periodic || sgn_r > 0) ? jr : psub(pk(R(0), R(0)), jr));
@@ -808,10 +799,10 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
                 int er = row, s = 1;
                 if (!periodic && row >= nr) er = map_row(p, row, -1, -1, s);
                 T dz, dr;
-                fd_both2<R>(sPsi + ((er - 2) & (DP - 1)) * SL, sPsi + ((er - 1) & (DP - 1)) * SL,
-                            sPsi + (er & (DP - 1)) * SL, sPsi + ((er + 1) & (DP - 1)) * SL,
-                            sPsi + ((er + 2) & (DP - 1)) * SL, dc + 2, dz, dr);
-                const int o = (row & (DD - 1)) * SD;
+                fd_both2<R>(sPsi + ((er - 2) & (DP - 1)) * WL, sPsi + ((er - 1) & (DP - 1)) * WL,
+                            sPsi + (er & (DP - 1)) * WL, sPsi + ((er + 1) & (DP - 1)) * WL,
+                            sPsi + ((er + 2) & (DP - 1)) * WL, dc + 2, dz, dr);
+                const int o = (row & (DD - 1)) * WD;
                 st2(sPz + o, dc, dz);
                 st2(sPr + o, dc, s > 0 ? dr : psub(pk(R(0), R(0)), dr));
             }
@@ -826,15 +817,15 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
                     er = map_row(p, row, -1, -1, s_ur);
                     s_uz = uz_top;
                 }
-                const int sj = (er & (DJ - 1)) * SU;
+                const int sj = (er & (DJ - 1)) * WU;
                 const T drho = ld2<T>(sRho + sj, uc);
                 const T rho = padd(drho, pk(rho_ref, rho_ref));
                 T fz = pmul(rho, pk(gz, gz)), fr = pk(R(0), R(0));
                 if (mp) {
                     const int c = uc + 4;
-                    const Tri<T> z0 = ld3<T>(sPsi + (er & (DP - 1)) * SL, c);
-                    const Tri<T> zm = ld3<T>(sPsi + ((er - 1) & (DP - 1)) * SL, c);
-                    const Tri<T> zq = ld3<T>(sPsi + ((er + 1) & (DP - 1)) * SL, c);
+                    const Tri<T> z0 = ld3<T>(sPsi + (er & (DP - 1)) * WL, c);
+                    const Tri<T> zm = ld3<T>(sPsi + ((er - 1) & (DP - 1)) * WL, c);
+                    const Tri<T> zq = ld3<T>(sPsi + ((er + 1) & (DP - 1)) * WL, c);
                     // Kupershtokh force, Eq. (kupershtokhforcing)
                     T s1z, s1r, s2z, s2r;
                     kup_moments2<R>(zm, z0, zq, s1z, s1r);
@@ -846,9 +837,9 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
                     if (ax) {
                         // F_axis, Eq. (multiphasecorrections); psi_rr = D_r(psi_r), psi_rz = D_r(psi_z)
                         const int cd = uc + 2;
-                        const int o2m = ((er - 2) & (DD - 1)) * SD, o1m = ((er - 1) & (DD - 1)) * SD;
-                        const int o1p = ((er + 1) & (DD - 1)) * SD, o2p = ((er + 2) & (DD - 1)) * SD;
-                        const int o0 = (er & (DD - 1)) * SD;
+                        const int o2m = ((er - 2) & (DD - 1)) * WD, o1m = ((er - 1) & (DD - 1)) * WD;
+                        const int o1p = ((er + 1) & (DD - 1)) * WD, o2p = ((er + 2) & (DD - 1)) * WD;
+                        const int o0 = (er & (DD - 1)) * WD;
                         const T prr = fd_r2<R, T>(sPr + o2m, sPr + o1m, sPr + o1p, sPr + o2p, cd);
                         const T prz = fd_r2<R, T>(sPz + o2m, sPz + o1m, sPz + o1p, sPz + o2p, cd);
                         const T psz = ld2<T>(sPz + o0, cd), psr = ld2<T>(sPr + o0, cd);
@@ -866,7 +857,7 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
                 }
                 const T irho = prcp<R>(rho);
                 const T half = pk(R(0.5), R(0.5));
-                const int ou = (row & (DU - 1)) * SU;
+                const int ou = (row & (DU - 1)) * WU;
                 const T vz = pmul(pfma(half, fz, ld2<T>(sJz + sj, uc)), irho);
                 const T vr = pmul(pfma(half, fr, ld2<T>(sJr + sj, uc)), irho);
                 st2(sUz + ou, uc, s_uz > 0 ? vz : psub(pk(R(0), R(0)), vz));
@@ -890,20 +881,20 @@ __device__ __forceinline__ void march2(const Params<R>& p, const R* __restrict__
             }
             if (c_valid(row)) {
                 const int c = cc + 2;
-                const int sj = (row & (DJ - 1)) * SU;
+                const int sj = (row & (DJ - 1)) * WU;
                 const T drho = ld2<T>(sRho + sj, c);
                 const T rho = padd(drho, pk(rho_ref, rho_ref));
                 const T irho = prcp<R>(rho);
                 const T u0z = pmul(ld2<T>(sJz + sj, c), irho), u0r = pmul(ld2<T>(sJr + sj, c), irho);
-                const int ou = (row & (DU - 1)) * SU;
+                const int ou = (row & (DU - 1)) * WU;
                 const T uz = ld2<T>(sUz + ou, c), ur = ld2<T>(sUr + ou, c);
                 // EDM velocity shift F / rho from u = u0 + F / (2 rho)
                 const T two = pk(R(2), R(2));
                 const T u1z = pfma(two, psub(uz, u0z), u0z), u1r = pfma(two, psub(ur, u0r), u0r);
                 T Hz = pk(R(0), R(0)), Hr = Hz, m0 = Hz;
                 if (ax) {
-                    const int o2m = ((row - 2) & (DU - 1)) * SU, o1m = ((row - 1) & (DU - 1)) * SU;
-                    const int o1p = ((row + 1) & (DU - 1)) * SU, o2p = ((row + 2) & (DU - 1)) * SU;
+                    const int o2m = ((row - 2) & (DU - 1)) * WU, o1m = ((row - 1) & (DU - 1)) * WU;
+                    const int o1p = ((row + 1) & (DU - 1)) * WU, o2p = ((row + 2) & (DU - 1)) * WU;
                     const T duz_dr = fd_r2<R, T>(sUz + o2m, sUz + o1m, sUz + o1p, sUz + o2p, c);
                     T dur_dz, dur_dr;
                     fd_both2<R>(sUr + o2m, sUr + o1m, sUr + ou, sUr + o1p, sUr + o2p, c, dur_dz, dur_dr);
