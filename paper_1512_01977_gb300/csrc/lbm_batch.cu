@@ -19,6 +19,7 @@ struct lbm_axi_batch {
     std::vector<lbm_axi*> solves;
     std::vector<int> cur0;  // each solve's current buffer when the batch was made
     void* d_solves;         // BatchSolve<R>[n]
+    lbm::BatchTable<float>* h_table;  // FP32, n <= BatchTable::N: the descriptors as one kernel argument
     lbm::Tile* d_tiles;     // tile plan for (strip, grid)
     int* d_first;           // [ncta + 1]
     int ncta;
@@ -69,6 +70,10 @@ cudaError_t upload(lbm_axi_batch* b) {
         nz[i] = h->nz;
         nr[i] = h->nr;
     }
+    if constexpr (sizeof(R) == 4) {
+        if (b->h_table)
+            for (int i = 0; i < b->n; i++) b->h_table->s[i] = hs[i];
+    }
     const int slots = b->grid > 0 ? b->grid : Ops<R>::batch_resident_ctas(b->strip);
     if (slots <= 0) return cudaErrorInvalidConfiguration;
     std::vector<lbm::Tile> tiles;
@@ -108,6 +113,9 @@ cudaError_t upload_tables(lbm_axi_batch* b) {
 }
 
 cudaError_t launch(lbm_axi_batch* b, int parity) {
+    if (b->h_table)  // FP32, n <= BatchTable::N: parameters through the constant bank
+        return Ops<float>::step_table(*b->h_table, b->d_tiles, b->d_first, b->ncta, b->mp, b->ax, parity, b->strip,
+                                      b->d_err, b->stream);
     if (b->precision == 32)
         return Ops<float>::step_batch(static_cast<const BatchSolve<float>*>(b->d_solves), b->d_tiles, b->d_first,
                                       b->ncta, b->mp, b->ax, parity, b->strip, b->d_err, b->stream);
@@ -154,6 +162,7 @@ void release(lbm_axi_batch* b) {
     if (b->d_err) cudaFree(b->d_err);
     if (b->h_err) cudaFreeHost(b->h_err);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b->h_table;
 }
 
 // Time `trials` launches of fn on stream s (ms per launch), non-destructively.
@@ -204,6 +213,7 @@ int lbm_axi_batch_create(lbm_axi* const* solves, int n, void* stream, lbm_axi_ba
     b->ax = h0->opts.axis_terms != 0;
     b->device = dev;
     b->d_solves = nullptr;
+    b->h_table = nullptr;
     b->d_tiles = nullptr;
     b->d_first = nullptr;
     b->ncta = 0;
@@ -231,6 +241,13 @@ int lbm_axi_batch_create(lbm_axi* const* solves, int n, void* stream, lbm_axi_ba
             return LBM_ERR_CUDA;
         }
         b->cur0[i] = solves[i]->cur;
+    }
+    if (b->precision == 32 && n <= lbm::BatchTable<float>::N) {
+        b->h_table = new (std::nothrow) lbm::BatchTable<float>();
+        if (!b->h_table) {
+            delete b;
+            return LBM_ERR_OOM;
+        }
     }
     const size_t ssz = b->precision == 32 ? sizeof(BatchSolve<float>) : sizeof(BatchSolve<double>);
     bool ok = cudaMalloc(&b->d_solves, ssz * n) == cudaSuccess &&

@@ -89,6 +89,16 @@ struct BatchSolve {
     R* h_b;
 };
 
+// The descriptors of a batch of at most N solves as one kernel argument
+// (about 30 KB, under the 32 KB argument limit): the kernel reads a tile's
+// parameters through the constant bank instead of staging them in shared
+// memory.
+template <typename R>
+struct BatchTable {
+    static constexpr int N = (30 * 1024) / (int)sizeof(BatchSolve<R>);
+    BatchSolve<R> s[N];
+};
+
 // Compiled forms of the collision in the fused kernel (bit set): Guo forcing
 // in place of the EDM shift, the link-midpoint source in place of h_i at the node.
 enum { FV_GUO = 1, FV_LINK = 2 };

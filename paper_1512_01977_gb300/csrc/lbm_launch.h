@@ -58,6 +58,10 @@ struct Ops {
     // arithmetic as step_batch with a batch of one).
     static cudaError_t step_single(const BatchSolve<R>& solve, const Tile* tiles, const int* first, int ncta,
                                    bool mp, bool ax, int parity, int* err, cudaStream_t s, int fv = 0);
+    // The batched step with the descriptors as one kernel argument (FP32; n <=
+    // BatchTable<R>::N solves; cudaErrorNotSupported in FP64).
+    static cudaError_t step_table(const BatchTable<R>& table, const Tile* tiles, const int* first, int ncta,
+                                  bool mp, bool ax, int parity, int strip, int* err, cudaStream_t s);
     static int batch_resident_ctas(int strip);
     static size_t batch_smem(int strip);
 };

@@ -86,6 +86,8 @@ static cudaError_t set_step_attr(int smem) {
 
 template <typename R>
 static cudaError_t single_prepare();
+template <typename R, int TZ>
+static cudaError_t table_prepare();
 
 template <typename R>
 cudaError_t Ops<R>::prepare() {
@@ -105,6 +107,10 @@ cudaError_t Ops<R>::prepare() {
     if (e == cudaSuccess && (batch_resident_ctas(kStripNarrow) <= 0 || batch_resident_ctas(kStripWide) <= 0))
         e = cudaErrorInvalidConfiguration;
     if (e == cudaSuccess) e = single_prepare<R>();  // the single-solve form of the fused kernel
+    if constexpr (sizeof(R) == 4) {  // the argument-table form of the batched kernel
+        if (e == cudaSuccess) e = table_prepare<R, kStripNarrow>();
+        if (e == cudaSuccess) e = table_prepare<R, kStripWide>();
+    }
     return e;
 }
 
@@ -269,6 +275,51 @@ static cudaError_t batch_prepare() {
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     }
     return e;
+}
+
+template <typename R, int TZ, bool MP, bool AX>
+static auto table_kernel() {
+    return k_step_table<R, TZ, BatchTile<R, TZ>::RR, BatchTile<R, TZ>::CP, BatchTile<R, TZ>::MINB, MP, AX>;
+}
+
+template <typename R, int TZ>
+static cudaError_t table_prepare() {
+    const int smem = (int)BatchTile<R, TZ>::smem();
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(table_kernel<R, TZ, true, true>(), a, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(table_kernel<R, TZ, true, false>(), a, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(table_kernel<R, TZ, false, true>(), a, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(table_kernel<R, TZ, false, false>(), a, smem);
+    return e;
+}
+
+template <typename R, int TZ>
+static cudaError_t launch_table(const BatchTable<R>& table, const Tile* tiles, const int* first, int ncta, bool mp,
+                                bool ax, int parity, int* err, cudaStream_t s) {
+    using T = BatchTile<R, TZ>;
+    const size_t smem = T::smem();
+    if (mp && ax)
+        table_kernel<R, TZ, true, true>()<<<ncta, T::NT, smem, s>>>(table, tiles, first, parity, err);
+    else if (mp)
+        table_kernel<R, TZ, true, false>()<<<ncta, T::NT, smem, s>>>(table, tiles, first, parity, err);
+    else if (ax)
+        table_kernel<R, TZ, false, true>()<<<ncta, T::NT, smem, s>>>(table, tiles, first, parity, err);
+    else
+        table_kernel<R, TZ, false, false>()<<<ncta, T::NT, smem, s>>>(table, tiles, first, parity, err);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t Ops<R>::step_table(const BatchTable<R>& table, const Tile* tiles, const int* first, int ncta, bool mp,
+                               bool ax, int parity, int strip, int* err, cudaStream_t s) {
+    if constexpr (sizeof(R) == 4) {
+        if (ncta <= 0) return cudaErrorInvalidConfiguration;
+        return strip == kStripNarrow
+                   ? launch_table<R, kStripNarrow>(table, tiles, first, ncta, mp, ax, parity, err, s)
+                   : launch_table<R, kStripWide>(table, tiles, first, ncta, mp, ax, parity, err, s);
+    } else {
+        return cudaErrorNotSupported;
+    }
 }
 
 template <typename R>

@@ -1080,6 +1080,33 @@ __global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB)
     }
 }
 
+// The batched step with the solves' descriptors as one kernel argument
+// (batches of at most BatchTable<R>::N solves): a tile's parameters are read
+// through the constant bank by the tile's solve index instead of being staged
+// in shared memory (the same arithmetic, so the same results).
+template <typename R, int TZ, int RR, int CP, int MINB, bool MP, bool AX>
+__global__ void __launch_bounds__(StepShape<TZ, RR, CP>::NT, MINB)
+    k_step_table(const __grid_constant__ BatchTable<R> tab, const Tile* __restrict__ tiles,
+                 const int* __restrict__ first, int parity, int* __restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int skip;  // the solve already went unphysical: its populations are void, leave them
+    const int t1 = first[blockIdx.x + 1];
+    for (int t = first[blockIdx.x]; t < t1; t++) {
+        const Tile tl = tiles[t];
+        __syncthreads();  // everyone is done with the previous tile
+        if (threadIdx.x == 0) skip = *static_cast<volatile const int*>(err + tl.solve);
+        __syncthreads();
+        const BatchSolve<R>& s = tab.s[tl.solve];
+        const R* fin = parity ? s.f_b : s.f_a;
+        R* fo = parity ? const_cast<R*>(s.f_a) : s.f_b;
+        if (!skip) {
+            int bad = 0;
+            march_cp<R, TZ, RR, CP, MP, AX>(s.p, fin, fo, tl.strip, tl.j0, tl.jend, smem_raw, bad);
+            if (bad) atomicOr(&err[tl.solve], bad);
+        }
+    }
+}
+
 // The same step for a single solve, its descriptor passed by value: the
 // parameters are read from the kernel's constant bank instead of a shared-memory
 // copy per tile (fewer shared-memory loads on the bound pipe; the arithmetic,

@@ -70,6 +70,35 @@ def test_batch_equals_alone(lbm, precision, strip):
         s.close()
 
 
+def test_large_fp32_batch_equals_alone(lbm):
+    """An FP32 batch of 260 solves, more than one kernel-argument table holds
+    (256): the batched kernel then reads the descriptors from a device table;
+    every solve still equals its run alone, bitwise."""
+    n = 260
+    specs = I.batch_droplets(n=n, seed=9, lo=(24, 16), scale_max=1.6)
+    cases = []
+    for sp in specs:
+        c = Case(sp["nz"], sp["nr"], tau=1.0, T_over_Tc=0.85)
+        rv, rl = c.coexistence()
+        cases.append((c, I.droplet(c.nz, c.nr, min(sp["R"], 6.0), rl, rv), rv))
+    solvers = [c.solver(32, rr).init(*fields) for c, fields, rr in cases]
+    b = lbm.Batch(solvers)
+    assert b.step(21) == lbm.OK
+    assert b.status() == [lbm.OK] * n
+    b.close()
+    for k in range(0, n, 37):
+        c, fields, rr = cases[k]
+        s = c.solver(32, rr).init(*fields)
+        s.step(21)
+        ref = s.moments()
+        s.close()
+        m = solvers[k].moments()
+        for key in ("rho", "uz", "ur", "p"):
+            np.testing.assert_array_equal(m[key], ref[key])
+    for s in solvers:
+        s.close()
+
+
 @pytest.mark.parametrize("strip", [64, 112])
 def test_batch_fp64_matches_oracle(lbm, strip):
     """An FP64 batch whose mix holds grids wider than one strip (up to 230
