@@ -317,13 +317,25 @@ __global__ void __launch_bounds__(256) k_init(Params<R> p, double rho_ref, const
     const long long c = (long long)j * p.nz + k;
     const double d = rho[c];
     const double vz = uz ? uz[c] : 0.0, vr = ur ? ur[c] : 0.0;
-    const double usq = vz * vz + vr * vr;
+    if constexpr (sizeof(R) == 4) {
+        // FP32 deviations f_i - w_i rho_ref = w_i [(rho - rho_ref) + rho (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)]:
+        // rho - rho_ref in FP64, the velocity part in FP32 (FP64 arithmetic would set this kernel's time)
+        const float dr = (float)(d - rho_ref), rf = (float)d, zf = (float)vz, rrf = (float)vr;
+        const float usq = zf * zf + rrf * rrf;
 #pragma unroll
-    for (int i = 0; i < Q; i++) {
-        const double cu = cz_of(i) * vz + cr_of(i) * vr;
-        const double w = w_of<double>(i);
-        const double feq = w * d * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-        f[pull_slot(p, k, j, i)] = (R)(feq - w * rho_ref);
+        for (int i = 0; i < Q; i++) {
+            const float cu = (float)cz_of(i) * zf + (float)cr_of(i) * rrf;
+            f[pull_slot(p, k, j, i)] = w_of<float>(i) * (dr + rf * (3.0f * cu + 4.5f * cu * cu - 1.5f * usq));
+        }
+    } else {
+        const double usq = vz * vz + vr * vr;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const double cu = cz_of(i) * vz + cr_of(i) * vr;
+            const double w = w_of<double>(i);
+            const double feq = w * d * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+            f[pull_slot(p, k, j, i)] = (R)(feq - w * rho_ref);
+        }
     }
 }
 
