@@ -2,7 +2,8 @@
 grid sizes 17..259 x 16..47 (one to three z-strips, ragged last strips, rows
 that end at every offset of a tile), both wall tops, both kappa readings, and
 the four collision forms (EDM / Guo forcing, h_i at the node / link average);
-a droplet with a random flow, 40 steps, the FP64 bar of test_gpu_parity."""
+a droplet with a random flow, 40 steps: FP64 at the bar of test_gpu_parity,
+FP32 (deviations about rho_v) at the droplet bars of test_gpu_fp32."""
 import numpy as np
 import pytest
 
@@ -26,8 +27,9 @@ def _configs(n=24, seed=123):
         yield it, nz, nr, top, form, kappa
 
 
+@pytest.mark.parametrize("precision", [64, 32])
 @pytest.mark.parametrize("it,nz,nr,top,form,kappa", list(_configs()))
-def test_random_fp64_parity(it, nz, nr, top, form, kappa):
+def test_random_parity(it, nz, nr, top, form, kappa, precision):
     import torch
 
     if not torch.cuda.is_available():
@@ -42,13 +44,16 @@ def test_random_fp64_parity(it, nz, nr, top, form, kappa):
     _, vz, vr = I.random_state(nz, nr, 1.0, 0.0, 1e-3, it)
     ur = vr * (np.arange(nr) + 0.5)[:, None] / nr
     o = O.Oracle(c.oracle_params()).init(rho, vz, ur, physical=True).step(40)
-    s = c.solver().init(rho, vz, ur, physical=True)
+    s = c.solver(precision, rv if precision == 32 else 0.0).init(rho, vz, ur, physical=True)
     assert lbm.lbm_axi_get_tuning(s.h)[0] == lbm.PATH_FUSED
     s.step(40)
     mg, mo = s.moments(), o.moments()
     s.close()
     errs = {k: rel_err(mg[k], mo[k]) for k in ("rho", "p")}
     errs["u"] = vel_err(mg, mo)
-    errs.update(component_errs(mg, mo))
-    for k, e in errs.items():
-        assert e is None or e <= TOL64, (k, errs)
+    if precision == 64:
+        errs.update(component_errs(mg, mo))
+        for k, e in errs.items():
+            assert e is None or e <= TOL64, (k, errs)
+    else:
+        assert errs["rho"] <= 2e-4 and errs["u"] <= 1e-3 and errs["p"] <= 1e-3, errs
