@@ -97,3 +97,43 @@ def test_too_shallow_rings_are_caught(ring, depth):
             for periodic in (False, True):
                 for j0 in range(0, nr, 16):
                     _check_segment(nr, j0, min(j0 + 16, nr), periodic, 2, shallow)
+
+
+
+def _items(tz, rr, mapping):
+    """Per stage, the (thread, row offset, first column) of every active item of
+    the two-column march for strip width tz, as the kernel maps thread ids."""
+    widths = {"L": tz + 12, "D": tz + 8, "U": tz + 4, "C": tz}
+    nt = (rr * (tz + 12) // 2 + 31) // 32 * 32
+    out = {}
+    for st, w in widths.items():
+        h = w // 2
+        got = []
+        for tid in range(nt):
+            if mapping == "rows":
+                row, col, on = tid >> 6, 2 * (tid & 63), (tid & 63) < h
+            else:
+                row, col, on = tid // h, 2 * (tid % h), tid < rr * h
+            if on:
+                got.append((tid, row, col))
+        out[st] = (got, h)
+    return out, nt
+
+
+@pytest.mark.parametrize("tz,mapping", [(112, "rows"), (112, "packed"), (64, "packed"), (96, "packed")])
+def test_item_mapping_covers_each_pair_once(tz, mapping):
+    """Every (row, column pair) of every stage has exactly one thread, for the
+    warp-row mapping the kernel uses with 112-column strips (128 threads, rows of
+    at most 64 pairs on two whole warps each) and the packed mapping otherwise;
+    with the warp-row mapping no warp holds items of two rows."""
+    rr = 2
+    src = open(os.path.join(ROOT, "paper_1512_01977_gb300", "csrc", "lbm_step.cuh")).read()
+    assert "kWarpRows = S::NT == 128 && RR == 2 && HL <= 64;" in src  # the condition restated here
+    items, nt = _items(tz, rr, mapping)
+    if mapping == "rows":
+        assert nt == 128 and (tz + 12) // 2 <= 64
+    for st, (got, h) in items.items():
+        assert sorted((r, c) for _, r, c in got) == [(r, 2 * c) for r in range(rr) for c in range(h)], st
+        if mapping == "rows":
+            for w in range(nt // 32):
+                assert len({r for tid, r, _ in got if tid // 32 == w}) <= 1, (st, w)
